@@ -32,11 +32,8 @@ CUDA_UNITS = [
     "irgl_api.cu",
     "irgl_k_single.cu",
     "irgl_k_launch.cu",
-    "irgl_k_batch.cu",
 ]
-HOST_UNITS = [
-    "irgl_server.cpp",
-]
+HOST_UNITS: list[str] = []
 
 
 def _nvcc() -> str:

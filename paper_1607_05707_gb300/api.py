@@ -1,0 +1,152 @@
+"""Torch-facing convenience layer over the C-ABI binding (marshalling only).
+
+PyTorch supplies device memory and the CUDA stream; every traversal step runs in
+libirgl.so's kernels through the same-name functions of :mod:`.irgl`.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import irgl as C
+from .inputs import CSR
+
+
+def _np_ptr(a: np.ndarray | None) -> int | None:
+    return None if a is None else int(a.ctypes.data)
+
+
+class Graph:
+    """A CSR graph resident on the device (owned by the library)."""
+
+    def __init__(self, ctx: "Context", g: CSR, symmetric: bool | None = None, validate: bool = True):
+        self.ctx = ctx
+        self.n, self.m = g.n, g.m
+        self.symmetric = g.symmetric if symmetric is None else symmetric
+        flags = C.IRGL_HOST_PTRS | (C.IRGL_SYMMETRIC if self.symmetric else 0) | (C.IRGL_VALIDATE if validate else 0)
+        rp = np.ascontiguousarray(g.row_ptr, dtype=np.uint32)
+        col = np.ascontiguousarray(g.col, dtype=np.uint32)
+        w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.int32)
+        self.weighted = w is not None
+        self.handle = C.irgl_csr_load(ctx.handle, g.n, g.m, _np_ptr(rp), _np_ptr(col), _np_ptr(w), flags)
+
+    def close(self) -> None:
+        if self.handle:
+            C.irgl_graph_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Worklist:
+    def __init__(self, ctx: "Context", capacity: int):
+        self.ctx = ctx
+        self.capacity = capacity
+        self.handle = C.irgl_worklist_create(ctx.handle, capacity)
+
+    def push(self, items) -> None:
+        a = np.ascontiguousarray(np.atleast_1d(items), dtype=np.uint32)
+        C.irgl_worklist_push(self.handle, _np_ptr(a), a.size)
+
+    def push_range(self, k: int) -> None:
+        C.irgl_worklist_push_range(self.handle, k)
+
+    def clear(self) -> None:
+        C.irgl_worklist_clear(self.handle)
+
+    def size(self) -> int:
+        return C.irgl_worklist_size(self.handle)
+
+    def read(self) -> np.ndarray:
+        buf = np.empty(self.capacity, dtype=np.uint32)
+        n = C.irgl_worklist_read(self.handle, _np_ptr(buf), self.capacity)
+        return buf[: min(n, self.capacity)].copy()
+
+    def close(self) -> None:
+        if self.handle:
+            C.irgl_worklist_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """Device + stream binding (defaults to torch's current stream on ``device``)."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.handle = C.irgl_ctx_create(device, self.stream.cuda_stream)
+        self.sm_count, self.default_tuning = C.irgl_ctx_info(self.handle)
+
+    def load(self, g: CSR, symmetric: bool | None = None, validate: bool = True) -> Graph:
+        return Graph(self, g, symmetric, validate)
+
+    def worklist(self, capacity: int) -> Worklist:
+        return Worklist(self, capacity)
+
+    def state(self, n: int) -> torch.Tensor:
+        return torch.empty(max(n, 1), dtype=torch.int32, device=f"cuda:{self.device}")
+
+    def iterate(self, kernel: str, g: Graph, initial: Worklist | None, out: torch.Tensor | None = None,
+                mode: str = "persistent", tuning=None, max_rounds: int = 0) -> tuple[torch.Tensor, dict]:
+        out = self.state(g.n) if out is None else out
+        st = C.irgl_iterate(self.handle, C.KERNELS[kernel], g.handle, None if initial is None else initial.handle,
+                            out.data_ptr(), C.MODES[mode], tuning, max_rounds)
+        return out, st
+
+    def iterate_async(self, kernel: str, g: Graph, initial: Worklist | None, out: torch.Tensor,
+                      tuning=None, max_rounds: int = 0) -> None:
+        C.irgl_iterate_async(self.handle, C.KERNELS[kernel], g.handle, None if initial is None else initial.handle,
+                             out.data_ptr(), tuning, max_rounds)
+
+    def sync(self) -> dict:
+        return C.irgl_ctx_sync(self.handle)
+
+    def run(self, kernel: str, g: Graph, srcs=None, out: torch.Tensor | None = None, mode: str = "persistent",
+            tuning=None, max_rounds: int = 0) -> tuple[torch.Tensor, dict]:
+        """One query; result stays on the device (int32 view of the uint32 values)."""
+        out = self.state(g.n) if out is None else out
+        s = None if srcs is None else np.ascontiguousarray(np.atleast_1d(srcs), dtype=np.uint32)
+        st = C.irgl_run(self.handle, C.KERNELS[kernel], g.handle, _np_ptr(s), 0 if s is None else s.size,
+                        out.data_ptr(), 0, C.MODES[mode], tuning, max_rounds)
+        return out, st
+
+    def run_host(self, kernel: str, g: Graph, srcs=None, out: np.ndarray | None = None, mode: str = "persistent",
+                 tuning=None, max_rounds: int = 0) -> tuple[np.ndarray, dict]:
+        """One query with host buffers: sources in, uint32 result out (copies inside the call)."""
+        out = np.empty(g.n, dtype=np.uint32) if out is None else out
+        s = None if srcs is None else np.ascontiguousarray(np.atleast_1d(srcs), dtype=np.uint32)
+        st = C.irgl_run(self.handle, C.KERNELS[kernel], g.handle, _np_ptr(s), 0 if s is None else s.size,
+                        _np_ptr(out), 1, C.MODES[mode], tuning, max_rounds)
+        return out, st
+
+    def invoke(self, kernel: str, g: Graph, wl_in: Worklist, wl_out: Worklist, state: torch.Tensor, level: int = 0,
+               reduce: str = "any", tuning=None) -> int:
+        return C.irgl_invoke(self.handle, C.KERNELS[kernel], g.handle, wl_in.handle, wl_out.handle, state.data_ptr(),
+                             level, C.IRGL_REDUCE_ANY if reduce == "any" else C.IRGL_REDUCE_ALL, tuning)
+
+    def init_state(self, kernel: str, g: Graph, initial: Worklist | None, state: torch.Tensor) -> None:
+        C.irgl_init_state(self.handle, C.KERNELS[kernel], g.handle, None if initial is None else initial.handle,
+                          state.data_ptr())
+
+    def debug_set(self, key: int, value: int) -> None:
+        C.irgl_debug_set(self.handle, key, value)
+
+    def close(self) -> None:
+        if self.handle:
+            C.irgl_ctx_destroy(self.handle)
+            self.handle = 0
+
+
+def as_u32(t: torch.Tensor) -> np.ndarray:
+    """Device int32 tensor holding uint32 values -> host uint32 array."""
+    return t.detach().cpu().numpy().view(np.uint32)

@@ -1,0 +1,81 @@
+// Host-side object layouts shared by the translation units of libirgl.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+
+#include "irgl.h"
+#include "irgl_device.cuh"
+
+struct irgl_worklist;
+
+struct irgl_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  irgl::DevStatus* st = nullptr;       // device status block
+  irgl::DevStatus* st_host = nullptr;  // pinned mirror
+  uint32_t* ws_items[2] = {nullptr, nullptr};  // Iterate scratch worklists
+  uint32_t ws_cap = 0;
+  uint32_t* ws_stamp = nullptr;  // SSSP/CC push dedup stamps
+  uint32_t ws_stamp_n = 0;
+  uint32_t* ws_state = nullptr;  // result buffer of irgl_run with a host output
+  uint32_t ws_state_n = 0;
+  irgl_worklist* run_wl = nullptr;  // sources of irgl_run
+  std::unordered_map<int, int> occ;  // occupancy cache
+  // test hooks
+  uint64_t dbg_timeout_us = 0;
+  int dbg_skip_cta = -1;
+  uint32_t dbg_cap = 0;
+};
+
+struct irgl_graph {
+  irgl_ctx* ctx = nullptr;
+  uint32_t n = 0;
+  uint64_t m = 0;
+  uint32_t* row_ptr = nullptr;
+  uint32_t* col = nullptr;
+  int32_t* w = nullptr;
+  bool owns = false;
+  int flags = 0;
+  int32_t max_w = 0;
+};
+
+struct irgl_worklist {
+  irgl_ctx* ctx = nullptr;
+  uint32_t cap = 0;
+  uint32_t* items = nullptr;
+  uint32_t* tail = nullptr;     // device counter (own 128-byte line)
+  uint32_t* staging = nullptr;  // device copy of host items being pushed
+  uint32_t staging_n = 0;
+};
+
+namespace irgl {
+
+struct DeviceGuard {
+  explicit DeviceGuard(int dev);
+  ~DeviceGuard();
+  int prev_ = 0;
+  int dev_ = 0;
+};
+
+extern thread_local std::string g_last_error;
+irgl_status fail(irgl_status s, const char* fmt, ...);
+irgl_status cuda_fail(cudaError_t e, const char* what);
+irgl_tuning default_tuning();
+irgl_status resolve_tuning(const irgl_tuning* in, irgl_tuning* out);
+irgl_status read_status(irgl_ctx* ctx, DevStatus* out);
+void reset_status(irgl_ctx* ctx);
+irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp);
+int occupancy(irgl_ctx* ctx, int kind, uint32_t op, uint32_t cta, int red);
+uint32_t persistent_grid(irgl_ctx* ctx, uint32_t op, const irgl_tuning& t);
+irgl_status check_kernel_graph(irgl_kernel k, const irgl_graph* g);
+KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tuning& t);
+
+}  // namespace irgl
+
+irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_worklist* initial, uint32_t* state_dev,
+                         irgl_mode mode, const irgl_tuning* tin, uint32_t max_rounds, irgl_stats* stats, bool sync);

@@ -1,0 +1,275 @@
+"""ctypes binding of libirgl.so (the C-ABI declared in include/irgl.h).
+
+Argument marshalling only: every function here forwards to the C entry point
+of the same name and raises :class:`IrglError` on a non-zero status. Every step
+of the traversal runs in the library's CUDA kernels; there is no Python or CPU
+fallback, and loading fails loudly when libirgl.so has not been built.
+
+Pointers are passed as integers (``tensor.data_ptr()``, ``numpy.ctypes.data``);
+streams as ``torch.cuda.Stream.cuda_stream`` integers.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, c_char_p, c_int, c_int64, c_uint32, c_uint64, c_void_p
+
+from . import _build
+
+IRGL_OK = 0
+IRGL_ERR_INVALID_ARG = -1
+IRGL_ERR_OOM = -2
+IRGL_ERR_WL_OVERFLOW = -3
+IRGL_ERR_BARRIER_TIMEOUT = -4
+IRGL_ERR_CUDA = -5
+IRGL_ERR_NOT_SYMMETRIC = -6
+IRGL_ERR_ADMISSION = -7
+IRGL_ERR_MAX_ROUNDS = -8
+IRGL_ERR_NOT_READY = -9
+IRGL_ERR_UNSUPPORTED = -10
+
+IRGL_INF = 0xFFFFFFFF
+
+IRGL_BFS, IRGL_SSSP, IRGL_CC = 0, 1, 2
+IRGL_PER_LAUNCH, IRGL_PERSISTENT = 0, 1
+IRGL_REDUCE_ANY, IRGL_REDUCE_ALL = 0, 1
+
+IRGL_HOST_PTRS = 0x0
+IRGL_DEVICE_PTRS = 0x1
+IRGL_SYMMETRIC = 0x2
+IRGL_VALIDATE = 0x4
+
+KERNELS = {"bfs": IRGL_BFS, "sssp": IRGL_SSSP, "cc": IRGL_CC}
+MODES = {"per_launch": IRGL_PER_LAUNCH, "persistent": IRGL_PERSISTENT}
+
+
+class irgl_tuning(ctypes.Structure):
+    _fields_ = [
+        ("cta_size", c_uint32),
+        ("warp_thresh", c_uint32),
+        ("cta_thresh", c_uint32),
+        ("chunk", c_uint32),
+        ("blocks_per_sm", c_uint32),
+        ("max_blocks", c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class irgl_stats(ctypes.Structure):
+    _fields_ = [
+        ("rounds", c_uint32),
+        ("grid", c_uint32),
+        ("cta_size", c_uint32),
+        ("launches", c_uint32),
+        ("edges_scanned", c_uint64),
+        ("last_out", c_uint32),
+        ("reserved", c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+class IrglError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"irgl status {status}: {message}")
+        self.status = status
+
+
+_P = c_void_p  # opaque handles and raw pointers
+
+# name -> argtypes (every function returns int status unless listed in _RESTYPE)
+_SIGS = {
+    "irgl_last_error": [],
+    "irgl_status_string": [c_int],
+    "irgl_ctx_create": [c_int, _P, POINTER(_P)],
+    "irgl_ctx_destroy": [_P],
+    "irgl_ctx_set_stream": [_P, _P],
+    "irgl_ctx_info": [_P, POINTER(c_uint32), POINTER(irgl_tuning)],
+    "irgl_csr_validate": [c_uint32, c_uint64, _P, _P, _P, c_int],
+    "irgl_csr_load": [_P, c_uint32, c_uint64, _P, _P, _P, c_int, POINTER(_P)],
+    "irgl_graph_destroy": [_P],
+    "irgl_graph_info": [_P, POINTER(c_uint32), POINTER(c_uint64), POINTER(c_int)],
+    "irgl_worklist_create": [_P, c_uint32, POINTER(_P)],
+    "irgl_worklist_destroy": [_P],
+    "irgl_worklist_push": [_P, _P, c_uint32],
+    "irgl_worklist_push_range": [_P, c_uint32],
+    "irgl_worklist_clear": [_P],
+    "irgl_worklist_size": [_P, POINTER(c_uint32)],
+    "irgl_worklist_read": [_P, _P, c_uint32, POINTER(c_uint32)],
+    "irgl_init_state": [_P, c_int, _P, _P, _P],
+    "irgl_invoke": [_P, c_int, _P, _P, _P, _P, c_uint32, c_int, POINTER(irgl_tuning), POINTER(c_int)],
+    "irgl_iterate": [_P, c_int, _P, _P, _P, c_int, POINTER(irgl_tuning), c_uint32, POINTER(irgl_stats)],
+    "irgl_iterate_async": [_P, c_int, _P, _P, _P, POINTER(irgl_tuning), c_uint32],
+    "irgl_ctx_sync": [_P, POINTER(irgl_stats)],
+    "irgl_run": [_P, c_int, _P, _P, c_uint32, _P, c_int, c_int, POINTER(irgl_tuning), c_uint32, POINTER(irgl_stats)],
+    "irgl_debug_set": [_P, c_int, c_int64],
+}
+_RESTYPE = {"irgl_last_error": c_char_p, "irgl_status_string": c_char_p}
+
+_lib = None
+
+
+def lib():
+    """Load libirgl.so (built in place by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        path = _build.IRGL_LIB
+        if not path.exists():
+            raise ImportError(f"{path.name} is not built: run __graft_entry__.build() (no CPU fallback exists)")
+        L = ctypes.CDLL(str(path))
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = _RESTYPE.get(name, c_int)
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return sorted(_SIGS)
+
+
+def _check(rc: int) -> None:
+    if rc != IRGL_OK:
+        raise IrglError(rc, lib().irgl_last_error().decode(errors="replace"))
+
+
+def _tuning(t) -> ctypes.c_void_p | None:
+    if t is None:
+        return None
+    if isinstance(t, irgl_tuning):
+        return ctypes.byref(t)
+    tt = irgl_tuning()
+    for k, v in dict(t).items():
+        setattr(tt, k, int(v))
+    return ctypes.byref(tt)
+
+
+# ----------------------------------------------------------------------------- same-name wrappers
+
+def irgl_last_error() -> str:
+    return lib().irgl_last_error().decode(errors="replace")
+
+
+def irgl_status_string(status: int) -> str:
+    return lib().irgl_status_string(status).decode()
+
+
+def irgl_ctx_create(device: int = 0, cuda_stream: int | None = None) -> int:
+    h = _P()
+    _check(lib().irgl_ctx_create(device, cuda_stream, ctypes.byref(h)))
+    return h.value
+
+
+def irgl_ctx_destroy(ctx: int) -> None:
+    _check(lib().irgl_ctx_destroy(ctx))
+
+
+def irgl_ctx_set_stream(ctx: int, cuda_stream: int | None) -> None:
+    _check(lib().irgl_ctx_set_stream(ctx, cuda_stream))
+
+
+def irgl_ctx_info(ctx: int) -> tuple[int, dict]:
+    sm = c_uint32()
+    t = irgl_tuning()
+    _check(lib().irgl_ctx_info(ctx, ctypes.byref(sm), ctypes.byref(t)))
+    return int(sm.value), t.as_dict()
+
+
+def irgl_csr_validate(n: int, m: int, row_ptr: int, col: int, w: int | None, flags: int) -> None:
+    _check(lib().irgl_csr_validate(n, m, row_ptr, col, w, flags))
+
+
+def irgl_csr_load(ctx: int, n: int, m: int, row_ptr: int, col: int, w: int | None, flags: int) -> int:
+    h = _P()
+    _check(lib().irgl_csr_load(ctx, n, m, row_ptr, col, w, flags, ctypes.byref(h)))
+    return h.value
+
+
+def irgl_graph_destroy(g: int) -> None:
+    _check(lib().irgl_graph_destroy(g))
+
+
+def irgl_graph_info(g: int) -> tuple[int, int, int]:
+    n, m, f = c_uint32(), c_uint64(), c_int()
+    _check(lib().irgl_graph_info(g, ctypes.byref(n), ctypes.byref(m), ctypes.byref(f)))
+    return int(n.value), int(m.value), int(f.value)
+
+
+def irgl_worklist_create(ctx: int, capacity: int) -> int:
+    h = _P()
+    _check(lib().irgl_worklist_create(ctx, capacity, ctypes.byref(h)))
+    return h.value
+
+
+def irgl_worklist_destroy(wl: int) -> None:
+    _check(lib().irgl_worklist_destroy(wl))
+
+
+def irgl_worklist_push(wl: int, items_host: int, k: int) -> None:
+    _check(lib().irgl_worklist_push(wl, items_host, k))
+
+
+def irgl_worklist_push_range(wl: int, k: int) -> None:
+    _check(lib().irgl_worklist_push_range(wl, k))
+
+
+def irgl_worklist_clear(wl: int) -> None:
+    _check(lib().irgl_worklist_clear(wl))
+
+
+def irgl_worklist_size(wl: int) -> int:
+    n = c_uint32()
+    _check(lib().irgl_worklist_size(wl, ctypes.byref(n)))
+    return int(n.value)
+
+
+def irgl_worklist_read(wl: int, items_host: int, cap: int) -> int:
+    n = c_uint32()
+    _check(lib().irgl_worklist_read(wl, items_host, cap, ctypes.byref(n)))
+    return int(n.value)
+
+
+def irgl_init_state(ctx: int, kernel: int, g: int, initial: int | None, state_dev: int) -> None:
+    _check(lib().irgl_init_state(ctx, kernel, g, initial, state_dev))
+
+
+def irgl_invoke(ctx: int, kernel: int, g: int, wl_in: int, wl_out: int, state_dev: int, level: int,
+                reduce: int = IRGL_REDUCE_ANY, tuning=None) -> int:
+    res = c_int()
+    _check(lib().irgl_invoke(ctx, kernel, g, wl_in, wl_out, state_dev, level, reduce, _tuning(tuning),
+                             ctypes.byref(res)))
+    return int(res.value)
+
+
+def irgl_iterate(ctx: int, kernel: int, g: int, initial: int | None, state_dev: int, mode: int = IRGL_PERSISTENT,
+                 tuning=None, max_rounds: int = 0) -> dict:
+    st = irgl_stats()
+    _check(lib().irgl_iterate(ctx, kernel, g, initial, state_dev, mode, _tuning(tuning), max_rounds,
+                              ctypes.byref(st)))
+    return st.as_dict()
+
+
+def irgl_iterate_async(ctx: int, kernel: int, g: int, initial: int | None, state_dev: int, tuning=None,
+                       max_rounds: int = 0) -> None:
+    _check(lib().irgl_iterate_async(ctx, kernel, g, initial, state_dev, _tuning(tuning), max_rounds))
+
+
+def irgl_ctx_sync(ctx: int) -> dict:
+    st = irgl_stats()
+    _check(lib().irgl_ctx_sync(ctx, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def irgl_run(ctx: int, kernel: int, g: int, srcs_host: int | None, nsrc: int, state: int, state_on_host: int,
+             mode: int = IRGL_PERSISTENT, tuning=None, max_rounds: int = 0) -> dict:
+    st = irgl_stats()
+    _check(lib().irgl_run(ctx, kernel, g, srcs_host, nsrc, state, state_on_host, mode, _tuning(tuning), max_rounds,
+                          ctypes.byref(st)))
+    return st.as_dict()
+
+
+def irgl_debug_set(ctx: int, key: int, value: int) -> None:
+    _check(lib().irgl_debug_set(ctx, key, value))

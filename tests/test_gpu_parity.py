@@ -1,0 +1,317 @@
+"""GPU parity: the CUDA path through the C-ABI vs the CPU oracle, bit-exact.
+
+Levels, distances and labels are uint32 fixed points, so the comparison is
+element-by-element equality (tolerance 0) under every schedule: thread/warp/CTA
+thresholds, CTA sizes, chunk sizes, grid sizes and both Iterate modes.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_05707_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+INF = 0xFFFFFFFF
+
+MODES = ("persistent", "per_launch")
+SCHEDULES = [
+    None,
+    dict(cta_size=128, warp_thresh=1, cta_thresh=1),          # every list to the whole CTA
+    dict(cta_size=256, warp_thresh=1, cta_thresh=1 << 30),    # every list to a warp
+    dict(cta_size=512, warp_thresh=1 << 30, cta_thresh=1 << 30),  # every list through the scan bin
+    dict(cta_size=1024, warp_thresh=4, cta_thresh=64, chunk=3),
+    dict(cta_size=256, warp_thresh=8, cta_thresh=128, chunk=2, max_blocks=3),
+    dict(cta_size=128, warp_thresh=16, cta_thresh=512, max_blocks=1),
+]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_05707_gb300.api import Context
+
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def run(ctx, kernel, g, dg, srcs, mode="persistent", tuning=None):
+    from paper_1607_05707_gb300.api import as_u32
+
+    out, st = ctx.run(kernel, dg, None if kernel == "cc" else srcs, mode=mode, tuning=tuning)
+    return as_u32(out)[: g.n], st
+
+
+def check(ctx, kernel, g, dg, srcs, mode="persistent", tuning=None):
+    got, st = run(ctx, kernel, g, dg, srcs, mode, tuning)
+    want = oracle.run(kernel, g, srcs)
+    if not np.array_equal(got, want):
+        bad = np.flatnonzero(got != want)
+        raise AssertionError(f"{kernel}/{mode}/{tuning}: {bad.size} of {g.n} differ; first {bad[:8]} "
+                             f"got {got[bad[:8]]} want {want[bad[:8]]}")
+    return st
+
+
+def tiny_graph(rng, n, p, symmetric):
+    src, dst = np.nonzero(rng.random((n, n)) < p)
+    w = rng.integers(0, 101, size=src.size)
+    if src.size:
+        k = int(rng.integers(0, 3))
+        src = np.concatenate([src, src[:k], [0]])
+        dst = np.concatenate([dst, dst[:k], [0]])
+        w = np.concatenate([w, w[:k] + 1, [5]])
+    if symmetric:
+        src, dst, w = np.concatenate([src, dst]), np.concatenate([dst, src]), np.concatenate([w, w])
+    return inputs.csr_from_edges(n, src, dst, w, symmetric=symmetric)
+
+
+# ----------------------------------------------------------------------------- small cases
+
+def test_tiny_random_graphs(ctx):
+    rng = np.random.default_rng(3)
+    for trial in range(40):
+        n = int(rng.integers(1, 200))
+        sym = bool(trial % 2)
+        g = tiny_graph(rng, n, float(rng.choice([0.01, 0.05, 0.2])), sym)
+        dg = ctx.load(g)
+        srcs = rng.integers(0, n, size=int(rng.integers(1, 5))).astype(np.uint32)
+        for mode in MODES:
+            check(ctx, "bfs", g, dg, srcs, mode)
+            check(ctx, "sssp", g, dg, srcs, mode)
+            if sym:
+                check(ctx, "cc", g, dg, srcs, mode)
+        dg.close()
+
+
+def test_special_shapes(ctx):
+    n = 300
+    path = inputs.csr_from_edges(n, np.arange(n - 1), np.arange(1, n), np.arange(1, n) % 7)
+    star = inputs.csr_from_edges(2001, np.zeros(2000, int), np.arange(1, 2001), np.full(2000, 3))
+    iso = inputs.csr_from_edges(10, [0, 9], [1, 8], [1, 1])
+    e = [(0, 1), (1, 2), (2, 0), (2, 3)]
+    s = [a for a, b in e] + [b for a, b in e]
+    d = [b for a, b in e] + [a for a, b in e]
+    two = inputs.csr_from_edges(8, s + [x + 4 for x in s], d + [x + 4 for x in d], np.ones(16), symmetric=True)
+    multi = inputs.csr_from_edges(3, [0, 0, 0, 1, 1, 2], [1, 1, 0, 1, 2, 2], [9, 2, 0, 1, 5, 4])
+    empty = inputs.csr_from_edges(5, [], [], [])
+    one = inputs.csr_from_edges(1, [], [], [])
+    for g, srcs in [(path, [0]), (path, [150]), (star, [0]), (star, [7]), (iso, [1]), (iso, [0, 9]),
+                    (two, [1]), (multi, [0]), (empty, [3]), (one, [0])]:
+        dg = ctx.load(g)
+        srcs = np.array(srcs, dtype=np.uint32)
+        for mode in MODES:
+            for tuning in (None, SCHEDULES[1], SCHEDULES[3]):
+                check(ctx, "bfs", g, dg, srcs, mode, tuning)
+                check(ctx, "sssp", g, dg, srcs, mode, tuning)
+        dg.close()
+    for g in (two, empty, one, inputs.csr_from_edges(4, [1, 2], [2, 1], [1, 1], symmetric=True)):
+        dg = ctx.load(g, symmetric=True)
+        for mode in MODES:
+            check(ctx, "cc", g, dg, None, mode)
+        dg.close()
+
+
+def test_grid64_closed_form(ctx):
+    g, srcs = inputs.workload_grid64()
+    dg = ctx.load(g)
+    r, c = np.divmod(np.arange(g.n), 64)
+    for mode in MODES:
+        got, st = run(ctx, "bfs", g, dg, srcs, mode)
+        np.testing.assert_array_equal(got, (r + c).astype(np.uint32))
+        assert st["rounds"] == 127
+        check(ctx, "cc", g, dg, srcs, mode)
+    dg.close()
+
+
+@pytest.mark.parametrize("tuning", SCHEDULES)
+def test_schedule_independence_rmat(ctx, tuning):
+    g = inputs.rmat(15, 16, seed=41, weights=True)
+    dg = ctx.load(g)
+    srcs = inputs.sources(g, 2, seed=42)
+    for s in srcs:
+        for mode in MODES:
+            check(ctx, "bfs", g, dg, np.array([s], np.uint32), mode, tuning)
+            check(ctx, "sssp", g, dg, np.array([s], np.uint32), mode, tuning)
+    check(ctx, "bfs", g, dg, srcs, "persistent", tuning)
+    check(ctx, "sssp", g, dg, srcs, "persistent", tuning)
+    dg.close()
+
+
+@pytest.mark.parametrize("tuning", SCHEDULES[:4])
+def test_mesh_bfs_cc(ctx, tuning):
+    g = inputs.mesh(300, 257, seed=9, del_frac=0.01, extra_frac=0.001, radius=8, weights=True)
+    dg = ctx.load(g)
+    for mode in MODES:
+        check(ctx, "bfs", g, dg, np.array([0], np.uint32), mode, tuning)
+        check(ctx, "cc", g, dg, None, mode, tuning)
+    check(ctx, "sssp", g, dg, np.array([1234], np.uint32), "persistent", tuning)
+    dg.close()
+
+
+def test_many_sources_init_path(ctx):
+    # more than eight initial items exercises the two-pass state initialisation
+    g = inputs.rmat(12, 8, seed=5, weights=True)
+    dg = ctx.load(g)
+    srcs = inputs.sources(g, 37, seed=6)
+    for mode in MODES:
+        check(ctx, "bfs", g, dg, srcs, mode)
+        check(ctx, "sssp", g, dg, srcs, mode)
+    dg.close()
+
+
+# ----------------------------------------------------------------------------- Invoke, reductions, worklists
+
+def test_invoke_bulk_synchronous_and_reductions(ctx):
+    from paper_1607_05707_gb300.api import as_u32
+
+    # 0 -> {1,2}, 1 -> {3}, 2 -> {}, 3 -> {0}
+    g = inputs.csr_from_edges(4, [0, 0, 1, 3], [1, 2, 3, 0], [1, 1, 1, 1])
+    dg = ctx.load(g)
+    a, b = ctx.worklist(16), ctx.worklist(16)
+    state = ctx.state(4)
+    a.push([0])
+    ctx.init_state("bfs", dg, a, state)
+    assert list(as_u32(state)) == [0, INF, INF, INF]
+    res = ctx.invoke("bfs", dg, a, b, state, level=0, reduce="any")
+    assert res == 1
+    assert a.size() == 0                      # in-worklist popped
+    assert sorted(b.read()) == [1, 2]         # pushes land in out only
+    assert list(as_u32(state)) == [0, 1, 1, INF]
+    # All: item 2 has no out-edges, so "every item pushed" is false
+    res = ctx.invoke("bfs", dg, b, a, state, level=1, reduce="all")
+    assert res == 0
+    assert sorted(a.read()) == [3]
+    # next round: 3 -> 0 (already visited) pushes nothing: Any = 0, All = 0
+    res = ctx.invoke("bfs", dg, a, b, state, level=2, reduce="any")
+    assert res == 0 and b.size() == 0
+    # reductions over an empty worklist: Any = false, All = true
+    assert ctx.invoke("bfs", dg, a, b, state, level=3, reduce="any") == 0
+    assert ctx.invoke("bfs", dg, a, b, state, level=3, reduce="all") == 1
+    # All = true when every popped item pushes
+    state2 = ctx.state(4)
+    a.clear(); b.clear()
+    a.push([0])
+    ctx.init_state("bfs", dg, a, state2)
+    assert ctx.invoke("bfs", dg, a, b, state2, level=0, reduce="all") == 1
+    for h in (a, b):
+        h.close()
+    dg.close()
+
+
+def test_iterate_with_worklist_object(ctx):
+    from paper_1607_05707_gb300.api import as_u32
+
+    g = inputs.rmat(13, 8, seed=11, weights=True)
+    dg = ctx.load(g)
+    srcs = inputs.sources(g, 3, seed=12)
+    wl = ctx.worklist(8)
+    wl.push(srcs)
+    for mode in MODES:
+        out, st = ctx.iterate("sssp", dg, wl, mode=mode)
+        np.testing.assert_array_equal(as_u32(out)[: g.n], oracle.sssp(g.n, g.row_ptr, g.col, g.w, srcs))
+        assert wl.size() == 3  # the initial worklist is read, not consumed
+    gs = inputs.mesh(40, 30, seed=3, del_frac=0.1)
+    dgs = ctx.load(gs)
+    allv = ctx.worklist(gs.n)
+    allv.push_range(gs.n)
+    out, _ = ctx.iterate("cc", dgs, allv)
+    np.testing.assert_array_equal(as_u32(out)[: gs.n], oracle.cc(gs.n, gs.row_ptr, gs.col))
+    wl.close(); allv.close(); dg.close(); dgs.close()
+
+
+def test_run_host_buffers(ctx):
+    g = inputs.rmat(14, 16, seed=21, weights=True)
+    dg = ctx.load(g)
+    s = inputs.sources(g, 1, seed=22)
+    for mode in MODES:
+        out, st = ctx.run_host("bfs", dg, s, mode=mode)
+        np.testing.assert_array_equal(out, oracle.bfs(g.n, g.row_ptr, g.col, s))
+        out, st = ctx.run_host("sssp", dg, s, mode=mode)
+        np.testing.assert_array_equal(out, oracle.sssp(g.n, g.row_ptr, g.col, g.w, s))
+        assert st["rounds"] > 1
+    dg.close()
+
+
+# ----------------------------------------------------------------------------- errors (host-made, no GPU fault)
+
+def test_errors_and_recovery(ctx):
+    from paper_1607_05707_gb300 import irgl as C
+
+    g = inputs.rmat(12, 16, seed=31, weights=True)
+    dg = ctx.load(g)
+    s = inputs.sources(g, 1, seed=32)
+    # worklist overflow: scratch worklists far too small
+    ctx.debug_set(3, 4)
+    for mode in MODES:
+        with pytest.raises(C.IrglError) as ei:
+            ctx.run("bfs", dg, s, mode=mode)
+        assert ei.value.status == C.IRGL_ERR_WL_OVERFLOW
+    ctx.debug_set(3, 0)
+    check(ctx, "bfs", g, dg, s)
+    # barrier timeout: one CTA never arrives, the others give up after 20 ms
+    ctx.debug_set(1, 20000)
+    ctx.debug_set(2, 1)
+    with pytest.raises(C.IrglError) as ei:
+        ctx.run("bfs", dg, s, mode="persistent")
+    assert ei.value.status == C.IRGL_ERR_BARRIER_TIMEOUT
+    ctx.debug_set(2, -1)
+    ctx.debug_set(1, 0)
+    check(ctx, "bfs", g, dg, s)
+    check(ctx, "sssp", g, dg, s)
+    # max_rounds (extra_cond): stops with a status, never a silent wrong answer
+    for mode in MODES:
+        with pytest.raises(C.IrglError) as ei:
+            ctx.run("bfs", dg, s, mode=mode, max_rounds=2)
+        assert ei.value.status == C.IRGL_ERR_MAX_ROUNDS
+    check(ctx, "sssp", g, dg, s, "per_launch")
+    # CC on a graph not loaded as symmetric
+    with pytest.raises(C.IrglError) as ei:
+        ctx.run("cc", dg, None)
+    assert ei.value.status == C.IRGL_ERR_NOT_SYMMETRIC
+    # SSSP without weights; source out of range
+    gu = inputs.grid(8)
+    dgu = ctx.load(gu)
+    with pytest.raises(C.IrglError) as ei:
+        ctx.run("sssp", dgu, [0])
+    assert ei.value.status == C.IRGL_ERR_INVALID_ARG
+    with pytest.raises(C.IrglError):
+        ctx.run("bfs", dgu, [64])
+    dgu.close()
+    dg.close()
+
+
+# ----------------------------------------------------------------------------- configuration sizes
+
+@pytest.mark.parametrize("mode", MODES)
+def test_rmat20_bfs_sssp_full(ctx, mode):
+    g, srcs = inputs.workload_rmat20(nsrc=3)
+    dg = ctx.load(g, validate=False)
+    for s in srcs[:2]:
+        one = np.array([s], np.uint32)
+        check(ctx, "bfs", g, dg, one, mode)
+        check(ctx, "sssp", g, dg, one, mode)
+    dg.close()
+
+
+def test_mesh4096_bfs_full(ctx):
+    g, srcs = inputs.workload_mesh(4096)
+    dg = ctx.load(g, validate=False)
+    st = check(ctx, "bfs", g, dg, srcs, "persistent")
+    lv = oracle.bfs(g.n, g.row_ptr, g.col, srcs)
+    # one round per BFS level, plus the last round that pushes nothing
+    assert st["rounds"] == int(lv[lv != INF].max()) + 1
+    assert st["rounds"] > 4000
+    dg.close()
+
+
+def test_batch_config_instances_sssp(ctx):
+    # the per-instance (one query per launch) form of the batched workload, on a sample
+    for g, srcs in inputs.workload_batch(count=12):
+        dg = ctx.load(g, validate=False)
+        check(ctx, "sssp", g, dg, srcs, "persistent")
+        dg.close()
