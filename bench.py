@@ -46,13 +46,21 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["rmat20", "grid64", "mesh"], default="rmat20")
+    ap.add_argument("--workload", choices=["rmat20", "grid64", "mesh", "batch256", "serve"], default="rmat20")
+    ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrival rate (queries/s)")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: arrival window (s)")
+    ap.add_argument("--serve-scale", type=int, default=24, help="serve: R-MAT scale of the large graph")
+    ap.add_argument("--slots", type=int, default=1024, help="serve: concurrent query slots")
+    ap.add_argument("--epoch-rounds", type=int, default=32, help="serve: rounds per epoch")
+    ap.add_argument("--verify", type=int, default=32, help="serve: queries checked against the oracle")
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (rmat20 workload)")
     ap.add_argument("--mesh-side", type=int, default=4096)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--tuning", type=str, default="", help="JSON irgl_tuning overrides")
+    ap.add_argument("--trace", action="store_true", help="print a per-round trace of one query per kernel to stderr")
     return ap.parse_args()
 
 
@@ -329,12 +337,26 @@ def run_gpu(args, world, rank, local):
     used = [(args.warmup + i) % len(wls) for i in range(args.steps)]
     for i in range(args.warmup):
         launch_step(i % len(wls))
-    # reached-vertex and edge counts per (source, kernel), taken from the results outside the timed region
-    counts = {}
+    # reached-vertex and edge counts per (source, kernel), taken from the results outside the timed region;
+    # edges scanned (re-relaxations included) from the device counters, one query at a time
+    counts, scanned = {}, {k: 0 for k in kernels}
     for j in sorted(set(used)):
-        launch_step(j)
         for k in kernels:
+            ctx.iterate_async(k, dg, wls[j], out[k], tuning=tuning)
+            scanned[k] += ctx.sync()["edges_scanned"]
             counts[(j, k)] = reached_stats(g, as_u32(out[k])[: g.n])
+    if args.trace and rank == 0:
+        C.irgl_trace_enable(ctx.handle, 1 << 16)
+        for k in kernels:
+            ctx.iterate_async(k, dg, wls[used[0]], out[k], tuning=tuning)
+            st = ctx.sync()
+            t, a, o = C.irgl_trace_read(ctx.handle)
+            print(f"# trace {k} source {srcs[used[0]]}: rounds={st['rounds']} total_us={(int(t[-1]) - int(t[0])) / 1e3:.1f}",
+                  file=sys.stderr)
+            for r in range(1, len(t)):
+                print(f"#  round {r - 1:5d} us {(int(t[r]) - int(t[r - 1])) / 1e3:9.2f} in {int(a[r]):9d} out {int(o[r]):9d}",
+                      file=sys.stderr)
+        C.irgl_trace_enable(ctx.handle, 0)
 
     rec = {k: [] for k in kernels}
     clocks = ClockSampler(local, enabled=(rank == 0 and not args.no_clocks))
@@ -365,7 +387,8 @@ def run_gpu(args, world, rank, local):
         nk = len(rec[k])
         per_kernel[k] = dict(time_s=tk, bytes=bk, launches=nk, achieved_gbs=bk / tk / 1e9,
                              gteps=sum(mR for (_, _, mR) in rec[k]) / tk / 1e9,
-                             us_per_launch=1e6 * tk / nk)
+                             us_per_launch=1e6 * tk / nk,
+                             work_inefficiency=scanned[k] / max(1, sum(counts[(j, k)][1] for j in set(used))))
     dom = max(kernels, key=lambda k: per_kernel[k]["time_s"])
     kname = {"bfs": "k_iterate<BFS>", "sssp": "k_iterate<SSSP>", "cc": "k_iterate<CC>"}[dom]
     pk = per_kernel[dom]
@@ -421,6 +444,229 @@ def run_gpu(args, world, rank, local):
     ctx.close()
 
 
+# ----------------------------------------------------------------------------- batched workload
+
+def run_batch(args, world, rank, local):
+    """256 independent SSSP instances (R-MAT scale 10..18, edge factor 8, 1-4 sources) in one
+    CUDA-graph-replayed persistent launch, against the same queries run one launch each."""
+    import torch
+
+    from paper_1607_05707_gb300.api import Batch, Context, as_u32
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    inst_all = inputs_workload_batch(args.instances)
+    inst = shard(inst_all, world, rank)
+    tuning = json.loads(args.tuning) if args.tuning else None
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context(local, stream)
+    dgs = [ctx.load(g, validate=False) for g, _ in inst]
+    b = Batch(ctx, max(len(inst), 1))
+    for (g, s), dg in zip(inst, dgs):
+        b.add("sssp", dg, s)
+    info = b.prepare(tuning, use_cuda_graph=True)
+    b.run()
+    mR = []
+    for q, (g, s) in enumerate(inst):
+        res, _ = b.result(q)
+        mR.append(reached_stats(g, res)[1])
+    edges = float(sum(mR))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        b.run()
+    clocks = ClockSampler(local, enabled=(rank == 0 and not args.no_clocks))
+    barrier(world)
+    times = []
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i)
+        torch.cuda.synchronize(dev)
+        st = b.run()
+        times.append(st["device_ms"] * 1e-3)
+    barrier(world)
+    clk = clocks.stop()
+    t_batch = max_over_ranks(sum(times) / len(times), world, dev)
+    value = sum_over_ranks(edges, world, dev) / t_batch / 1e9
+    # the same queries, one persistent launch each (host waits for each query's status)
+    outs = [ctx.state(g.n) for g, _ in inst]
+    wls = []
+    for (g, s) in inst:
+        wl = ctx.worklist(8)
+        wl.push(s)
+        wls.append(wl)
+    for q in range(min(8, len(inst))):
+        ctx.iterate_async("sssp", dgs[q], wls[q], outs[q], tuning=tuning)
+        ctx.sync()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    dev_sum = 0.0
+    for q in range(len(inst)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.iterate_async("sssp", dgs[q], wls[q], outs[q], tuning=tuning)
+        e1.record(stream)
+        ctx.sync()
+        dev_sum += e0.elapsed_time(e1) * 1e-3
+    t_seq = time.perf_counter() - t0
+    for q in range(len(inst)):  # same bytes out
+        if not np.array_equal(as_u32(outs[q])[: inst[q][0].n], b.result(q)[0]):
+            raise RuntimeError(f"batched result of instance {q} differs from its one-launch result")
+    seq_gteps = sum_over_ranks(edges, world, dev) / max_over_ranks(t_seq, world, dev) / 1e9
+    seq_dev_gteps = sum_over_ranks(edges, world, dev) / max_over_ranks(dev_sum, world, dev) / 1e9
+    # e2e: one batched run plus the copy of every instance's result to host memory
+    host = [np.empty(g.n, dtype=np.uint32) for g, _ in inst]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    b.run()
+    for q in range(len(inst)):
+        from paper_1607_05707_gb300 import irgl as C
+        C.irgl_batch_copy_result(b.handle, q, host[q].ctypes.data)
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = sum_over_ranks(edges, world, dev) / t_e2e / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        tt, ee, nq = 0.0, 0, 0
+        for (g, s), m in zip(inst, mR):
+            t1 = time.perf_counter()
+            oracle.sssp(g.n, g.row_ptr, g.col, g.w, s)
+            tt += time.perf_counter() - t1
+            ee += m
+            nq += 1
+            if tt > args.cpu_budget:
+                break
+        cpu = {"value": ee / tt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"first {nq} instances (serial Dijkstra), {tt:.1f} s on {platform.machine()} host"}
+    hbm, peak_src = peaks()
+    nbytes = sum(alg_bytes("sssp", g.n, int((b.result(q)[0] != INF).sum()), m) for q, ((g, _), m) in enumerate(zip(inst, mR)))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * t_batch, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict(workload=f"batch{args.instances}: SSSP instances, R-MAT scale U{{10..18}}, edge factor 8, "
+                                    f"1-4 sources, w in [1,100]; one CUDA-graph-replayed persistent launch",
+                           instances=len(inst_all), edges_out_of_reached=int(edges), batch=info,
+                           parallelism=f"instances sharded x{world}", l2="flushed between steps (512 MB write)",
+                           tuning=tuning or ctx.default_tuning),
+            "per_launch": {"gteps_wall": round(seq_gteps, 4), "gteps_device": round(seq_dev_gteps, 4),
+                           "form": "same instances, one persistent launch each, host waits per query"},
+            "batched_vs_per_launch": round(value / seq_gteps, 3),
+            "e2e": {"value": round(e2e, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(4 * sum(g.n for g, _ in inst))},
+            "gpu_launches": 3 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": round(nbytes / t_batch / 1e9, 2), "peak": hbm, "unit": "GB/s",
+                         "frac": round(nbytes / t_batch / 1e9 / hbm, 4), "traffic": measured_traffic("k_batch_iterate"),
+                         "kernel": "k_batch_iterate", "bytes_per_launch": int(nbytes)},
+            "cpu_baseline": cpu, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    b.close()
+
+
+def inputs_workload_batch(count):
+    from paper_1607_05707_gb300 import inputs
+
+    return inputs.workload_batch(count=count)
+
+
+# ----------------------------------------------------------------------------- serving workload
+
+def run_serve(args, world, rank, local):
+    """Poisson arrivals of BFS (70%) / SSSP (30%) queries with uniform sources against one R-MAT
+    graph and 32 grids of side U[256, 2048], served by the continuous-batching server."""
+    import threading
+
+    import torch
+
+    from paper_1607_05707_gb300 import inputs
+    from paper_1607_05707_gb300.api import Context, Server
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(2005)
+    graphs = [inputs.rmat(args.serve_scale, 16, seed=1005, weights=True)]
+    sides = rng.integers(256, 2049, size=32)
+    graphs += [inputs.mesh(int(sd), int(sd), seed=1005000 + i, weights=True) for i, sd in enumerate(sides)]
+    tuning = json.loads(args.tuning) if args.tuning else None
+    ctx = Context(local, torch.cuda.Stream(device=dev))
+    dgs = [ctx.load(g, validate=False) for g in graphs]
+    arrivals = inputs.poisson_arrivals(args.rate, args.duration, seed=2005 + rank)
+    nq = len(arrivals)
+    gi = rng.integers(0, len(graphs), size=nq)
+    kinds = np.where(rng.random(nq) < 0.7, "bfs", "sssp")
+    degs = [g.out_degree() for g in graphs]
+    srcs = np.empty(nq, dtype=np.int64)
+    for i in range(nq):
+        d = degs[gi[i]]
+        v = int(rng.integers(0, len(d)))
+        while d[v] == 0:
+            v = int(rng.integers(0, len(d)))
+        srcs[i] = v
+    verify = set(rng.choice(nq, size=min(args.verify, nq), replace=False).tolist())
+    bufs = {i: np.empty(graphs[gi[i]].n, dtype=np.uint32) for i in verify}
+    srv = Server(ctx, arena_bytes=0, max_slots=args.slots, epoch_rounds=args.epoch_rounds, count_edges=True,
+                 tuning=tuning)
+    # warm-up: a few queries before the clock starts
+    for i in range(min(8, nq)):
+        srv.submit(kinds[i], dgs[gi[i]], int(srcs[i]))
+    srv.drain(600)
+    base = srv.stats()
+    tickets = [0] * nq
+    clocks = ClockSampler(local, enabled=(rank == 0 and not args.no_clocks))
+    barrier(world)
+    t0 = time.perf_counter()
+    for i in range(nq):
+        dt = t0 + arrivals[i] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets[i] = srv.submit(kinds[i], dgs[gi[i]], int(srcs[i]), bufs.get(i))
+    srv.drain(3600)
+    t_total = time.perf_counter() - t0
+    clk = clocks.stop()
+    infos = [srv.poll(t) for t in tickets]
+    st = srv.stats()
+    lat = np.array([x["latency_s"] for x in infos])
+    edges = float(sum(x["edges"] for x in infos))
+    t_first = min(x["t_submit_s"] for x in infos)
+    t_last = max(x["t_done_s"] for x in infos)
+    span = max_over_ranks(t_last - t_first, world, dev)
+    value = sum_over_ranks(edges, world, dev) / span / 1e9
+    # bit-exact check of a sample against the oracle (after timing)
+    import oracle
+
+    bad = 0
+    for i in verify:
+        want = oracle.run(str(kinds[i]), graphs[gi[i]], np.array([srcs[i]], np.uint32))
+        bad += int(not np.array_equal(want, bufs[i]))
+    if bad:
+        raise RuntimeError(f"{bad} of {len(verify)} sampled served queries differ from the oracle")
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": nq,
+            "warmup": 8, "ms_per_step": round(1e3 * span / nq, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict(workload=f"serve: Poisson {args.rate:g} q/s for {args.duration:g} s, 70% BFS / 30% SSSP, "
+                                    f"R-MAT scale {args.serve_scale} (ef 16) + 32 grids of side U[256,2048]",
+                           queries=nq, slots=args.slots, epoch_rounds=args.epoch_rounds,
+                           arena_entries=st["arena_entries"], tuning=tuning or ctx.default_tuning,
+                           parallelism=f"replicas x{world} (independent arrival streams)"),
+            "latency": {"p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                        "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                        "max_ms": round(1e3 * float(lat.max()), 3)},
+            "server": {k: st[k] - base.get(k, 0) if k in ("completed", "epochs", "rounds", "edges") else st[k]
+                       for k in ("completed", "rejected", "epochs", "rounds", "edges", "busy_s", "grid", "cta_size")},
+            "verified_against_oracle": len(verify),
+            "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 4,
+                    "d2h_bytes_per_step": int(4 * np.mean([graphs[g].n for g in gi]))},
+            "wall_s": round(t_total, 3), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    srv.close()
+
+
 def main():
     args = parse_args()
     if args.warmup < 3:
@@ -428,6 +674,10 @@ def main():
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batch256":
+        run_batch(args, world, rank, local)
+    elif args.workload == "serve":
+        run_serve(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

@@ -83,7 +83,11 @@ typedef struct {
   uint32_t chunk;         /* worklist tiles (cta_size items each) taken per dynamic grab */
   uint32_t blocks_per_sm; /* persistent grid = min(this, occupancy) x SMs; 0 = occupancy */
   uint32_t max_blocks;    /* upper bound on the grid; 0 = none */
+  uint32_t flags;         /* IRGL_TUNE_NO_SPLIT: persistent kernels keep long lists in the CTA bin
+                             instead of splitting their edges over the whole grid */
 } irgl_tuning;
+
+#define IRGL_TUNE_NO_SPLIT 0x1u
 
 /* Per-call counters. */
 typedef struct {
@@ -93,7 +97,7 @@ typedef struct {
   uint32_t launches;      /* CUDA kernel launches issued by the call */
   uint64_t edges_scanned; /* adjacency entries read, re-relaxations included */
   uint32_t last_out;      /* size of the final out-worklist (0 when Iterate drained it) */
-  uint32_t reserved;
+  float device_ms;        /* CUDA-event time of the call's launches, when the call measures it (else 0) */
 } irgl_stats;
 
 /* ---------------------------------------------------------------- errors */
@@ -202,13 +206,130 @@ irgl_status irgl_run(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uint32_t
                      uint32_t* state, int state_on_host, irgl_mode mode, const irgl_tuning* t,
                      uint32_t max_rounds, irgl_stats* stats);
 
+/* ---------------------------------------------------------------- tracing
+ * Per-round trace of persistent launches on this context (Iterate and batch):
+ * after each round's grid barrier one thread records the globaltimer time
+ * (ns), the round's in-worklist size and its out-worklist size. Record 0 is
+ * the end of the prologue (state initialisation). irgl_trace_enable(ctx, 0)
+ * switches tracing off; enabling allocates 16 bytes per round of capacity.
+ * irgl_trace_read copies min(cap, rounds of the last launch + 1) records. */
+irgl_status irgl_trace_enable(irgl_ctx* ctx, uint32_t max_rounds);
+irgl_status irgl_trace_read(irgl_ctx* ctx, uint64_t* t_ns, uint32_t* in_n, uint32_t* out_n, uint32_t cap,
+                            uint32_t* nrec);
+
+/* ---------------------------------------------------------------- block sizes
+ * Sec. 4.4 rule for an outlined Pipe: the control kernel's block size must be
+ * in T_control = intersection over the Pipe's kernels of the block sizes each
+ * accepts. masks[i] is kernel i's set as a bitmask (bit b = CTA size 128 << b,
+ * b = 0..3). An empty intersection returns IRGL_ERR_UNSUPPORTED (no
+ * outlining); otherwise *out = preferred if it is in the set, else the
+ * highest size in the set (preferred = 0: always the highest). */
+irgl_status irgl_control_cta(const uint32_t* masks, uint32_t count, uint32_t preferred, uint32_t* out);
+
+/* ---------------------------------------------------------------- autotuning
+ * Coordinate descent over the irgl_tuning fields (CTA size, CTA and warp
+ * degree thresholds, chunk, CTAs per SM), each candidate timed as the median
+ * CUDA-event time of `reps` persistent Iterate runs of kernel k from the given
+ * sources on graph g (after one warm-up run). *best receives the fastest
+ * tuning and *best_ms its time. Results do not depend on the tuning (the
+ * fixed point is unique); only the time does. */
+irgl_status irgl_autotune(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uint32_t* srcs_host, uint32_t nsrc,
+                          uint32_t reps, irgl_tuning* best, float* best_ms);
+
+/* ---------------------------------------------------------------- batching
+ * A batch runs many independent queries ("instances": a graph, a kernel and
+ * its sources) in ONE persistent cooperative launch. Each instance owns a
+ * range of a device state arena (its result), its worklist items travel on the
+ * shared double-buffered worklist as arena offsets that a sorted offset table
+ * maps back to the instance, and its termination flag is the round of its
+ * last push. Instances may differ in graph, size and kernel; the CTA size is
+ * chosen by the T_control rule above. irgl_batch_prepare allocates the arena
+ * (16 bytes per instance vertex), uploads the descriptors and, with
+ * use_cuda_graph = 1, captures the whole launch sequence (admission kernels +
+ * persistent kernel) in a CUDA graph that irgl_batch_launch replays (if the
+ * capture fails the sequence is launched directly; irgl_batch_info tells).
+ * Every launch recomputes all instances from their sources.
+ * Queries are added before prepare; query ids are 0, 1, ... in add order. */
+irgl_status irgl_batch_create(irgl_ctx* ctx, uint32_t max_queries /* <= 1024 */, irgl_batch** out);
+irgl_status irgl_batch_destroy(irgl_batch* b);
+irgl_status irgl_batch_add(irgl_batch* b, irgl_graph* g, irgl_kernel k, const uint32_t* srcs_host, uint32_t nsrc,
+                           uint32_t* query_id);
+irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* t, int use_cuda_graph);
+/* Enqueue one run (events bracket it); irgl_batch_sync waits, checks the device
+ * status and fills stats (device_ms = event time of the run). */
+irgl_status irgl_batch_launch(irgl_batch* b);
+irgl_status irgl_batch_sync(irgl_batch* b, irgl_stats* stats);
+irgl_status irgl_batch_run(irgl_batch* b, irgl_stats* stats); /* launch + sync */
+irgl_status irgl_batch_info(irgl_batch* b, uint32_t* nqueries, uint32_t* grid, uint32_t* cta_size, int* graph_captured,
+                            uint64_t* arena_entries);
+/* Device pointer to query q's result (n entries, valid until the next launch or
+ * destroy) and the rounds that query was active (from its termination flag). */
+irgl_status irgl_batch_result(irgl_batch* b, uint32_t query_id, uint32_t** state_dev, uint32_t* n, uint32_t* rounds);
+irgl_status irgl_batch_copy_result(irgl_batch* b, uint32_t query_id, uint32_t* host_out);
+/* Autotune a prepared batch: the same coordinate descent, each candidate timed
+ * as the median event time of `reps` whole-batch runs (the batch is re-prepared
+ * per candidate, with the CUDA-graph choice it was prepared with). The batch is
+ * left prepared with the best tuning. */
+irgl_status irgl_batch_autotune(irgl_batch* b, uint32_t reps, irgl_tuning* best, float* best_ms);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching server for BFS/SSSP queries against device-resident
+ * graphs. A worker thread admits queued queries in arrival order while a
+ * slot is free and the query's state fits the device arena (16 bytes per
+ * vertex of its graph; first-fit), launches epochs of the batched persistent
+ * kernel (at most epoch_rounds rounds over every active query), and retires
+ * the queries that finished: their result is copied to the caller's host
+ * buffer (if one was given), and their memory and slot are reused. Queries
+ * that arrive while others run join the next epoch; their work overlaps on
+ * the device. Submission is thread-safe. */
+typedef struct {
+  uint64_t arena_bytes;   /* device budget for query state; 0 = 40% of the free HBM at creation */
+  uint32_t max_slots;     /* concurrently active queries, 1..1024 */
+  uint32_t epoch_rounds;  /* rounds per persistent launch */
+  uint32_t count_edges;   /* 1: count out-edges of reached vertices per query (for GTEPS) */
+  uint32_t reserved;
+  irgl_tuning tuning;     /* launch choices of the batched kernel (zeros = defaults) */
+} irgl_server_config;
+
+typedef struct {
+  int32_t status;     /* IRGL_OK or the error that ended the query */
+  uint32_t rounds;    /* rounds the query was active */
+  double latency_s;   /* submission -> result in the host buffer */
+  double t_submit_s;  /* host steady-clock times */
+  double t_done_s;
+  uint64_t edges;     /* out-edges of reached vertices (count_edges = 1) */
+} irgl_query_info;
+
+typedef struct {
+  uint64_t submitted, completed, rejected, epochs, rounds, edges;
+  double busy_s;      /* worker time spent in epochs */
+  uint32_t active, queued;
+  uint64_t arena_entries;
+  uint32_t grid, cta_size;
+} irgl_server_counters;
+
+irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irgl_server** out);
+/* host_out: NULL or a host array of the graph's n entries that receives the
+ * result (it must stay valid until the query completes). Returns
+ * IRGL_ERR_ADMISSION if the query can never fit the arena. */
+irgl_status irgl_server_submit(irgl_server* s, irgl_graph* g, irgl_kernel k, uint32_t src, uint32_t* host_out,
+                               uint64_t* ticket);
+/* IRGL_OK and *info when finished, IRGL_ERR_NOT_READY otherwise. */
+irgl_status irgl_server_poll(irgl_server* s, uint64_t ticket, irgl_query_info* info);
+/* Wait until every submitted query finished (IRGL_ERR_NOT_READY on timeout). */
+irgl_status irgl_server_drain(irgl_server* s, uint32_t timeout_ms);
+irgl_status irgl_server_stats(irgl_server* s, irgl_server_counters* out);
+irgl_status irgl_server_destroy(irgl_server* s);
+
 /* ---------------------------------------------------------------- test hooks
  * Fault injection on the host side only (no device fault is ever raised):
  *   key 1: barrier time limit in microseconds (0 = default 2 s)
  *   key 2: index of a CTA that skips its first grid-barrier arrival
  *          (-1 = none) -- the other CTAs then time out and report
  *          IRGL_ERR_BARRIER_TIMEOUT.
- *   key 3: override the capacity of the Iterate scratch worklists (0 = n). */
+ *   key 3: override the capacity of the Iterate scratch worklists (0 = n).
+ *   key 4: cap the big list of persistent Iterate launches (0 = default), so
+ *          long lists beyond the cap take the CTA-bin path. */
 irgl_status irgl_debug_set(irgl_ctx* ctx, int key, int64_t value);
 
 #ifdef __cplusplus

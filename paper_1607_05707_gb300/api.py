@@ -150,3 +150,74 @@ class Context:
 def as_u32(t: torch.Tensor) -> np.ndarray:
     """Device int32 tensor holding uint32 values -> host uint32 array."""
     return t.detach().cpu().numpy().view(np.uint32)
+
+
+class Batch:
+    """Many queries in one persistent launch (optionally replayed from a CUDA graph)."""
+
+    def __init__(self, ctx: Context, max_queries: int = 1024):
+        self.ctx = ctx
+        self.handle = C.irgl_batch_create(ctx.handle, max_queries)
+        self.sizes: list[int] = []
+
+    def add(self, kernel: str, g: Graph, srcs=None) -> int:
+        s = None if srcs is None else np.ascontiguousarray(np.atleast_1d(srcs), dtype=np.uint32)
+        q = C.irgl_batch_add(self.handle, g.handle, C.KERNELS[kernel], _np_ptr(s), 0 if s is None else s.size)
+        self.sizes.append(g.n)
+        return q
+
+    def prepare(self, tuning=None, use_cuda_graph: bool = True) -> dict:
+        C.irgl_batch_prepare(self.handle, tuning, 1 if use_cuda_graph else 0)
+        return C.irgl_batch_info(self.handle)
+
+    def launch(self) -> None:
+        C.irgl_batch_launch(self.handle)
+
+    def sync(self) -> dict:
+        return C.irgl_batch_sync(self.handle)
+
+    def run(self) -> dict:
+        return C.irgl_batch_run(self.handle)
+
+    def result(self, q: int) -> tuple[np.ndarray, int]:
+        """Host copy of query q's result and the rounds it was active."""
+        _, n, rounds = C.irgl_batch_result(self.handle, q)
+        out = np.empty(max(n, 1), dtype=np.uint32)
+        C.irgl_batch_copy_result(self.handle, q, _np_ptr(out))
+        return out[:n], rounds
+
+    def close(self) -> None:
+        if self.handle:
+            C.irgl_batch_destroy(self.handle)
+            self.handle = 0
+
+
+def trace(ctx: Context):
+    """(t_ns, in_n, out_n) per round of the context's last persistent launch (tracing must be enabled)."""
+    return C.irgl_trace_read(ctx.handle)
+
+
+class Server:
+    """Continuous-batching query server over device-resident graphs."""
+
+    def __init__(self, ctx: Context, arena_bytes: int = 0, max_slots: int = 256, epoch_rounds: int = 64,
+                 count_edges: bool = True, tuning=None):
+        self.ctx = ctx
+        self.handle = C.irgl_server_create(ctx.handle, arena_bytes, max_slots, epoch_rounds, int(count_edges), tuning)
+
+    def submit(self, kernel: str, g: Graph, src: int, out: np.ndarray | None = None) -> int:
+        return C.irgl_server_submit(self.handle, g.handle, C.KERNELS[kernel], int(src), _np_ptr(out))
+
+    def poll(self, ticket: int) -> dict | None:
+        return C.irgl_server_poll(self.handle, ticket)
+
+    def drain(self, timeout_s: float = 600.0) -> None:
+        C.irgl_server_drain(self.handle, int(timeout_s * 1000))
+
+    def stats(self) -> dict:
+        return C.irgl_server_stats(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            C.irgl_server_destroy(self.handle)
+            self.handle = 0

@@ -51,12 +51,13 @@ DeviceGuard::~DeviceGuard() {
 
 irgl_tuning default_tuning() {
   irgl_tuning t;
-  t.cta_size = 256;
+  t.cta_size = 128;
   t.warp_thresh = 32;
-  t.cta_thresh = 1024;
+  t.cta_thresh = 32;
   t.chunk = 1;
   t.blocks_per_sm = 0;
   t.max_blocks = 0;
+  t.flags = 0;
   return t;
 }
 
@@ -69,6 +70,7 @@ irgl_status resolve_tuning(const irgl_tuning* in, irgl_tuning* out) {
     if (in->chunk) d.chunk = in->chunk;
     d.blocks_per_sm = in->blocks_per_sm;
     d.max_blocks = in->max_blocks;
+    d.flags = in->flags;
   }
   if (!valid_cta(d.cta_size)) return fail(IRGL_ERR_INVALID_ARG, "cta_size must be 128, 256, 512 or 1024");
   if (d.chunk > 64) return fail(IRGL_ERR_INVALID_ARG, "chunk must be <= 64");
@@ -121,7 +123,29 @@ void reset_status(irgl_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
 }
 
+// Big-list entries: at most one per popped vertex of a round, capped (a full
+// list sends further long lists to the CTA bin, which is still correct).
+uint32_t big_capacity(uint64_t n) { return static_cast<uint32_t>(std::min<uint64_t>(std::max<uint64_t>(n, 1), 1u << 22)); }
+
+cudaError_t alloc_big(uint32_t cap, uint4** e, unsigned long long** off) {
+  cudaError_t r = cudaMalloc(e, sizeof(uint4) * (size_t)cap);
+  if (r == cudaSuccess) r = cudaMalloc(off, sizeof(unsigned long long) * (size_t)cap);
+  return r;
+}
+
 irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp) {
+  const uint32_t bcap = big_capacity(n);
+  if (bcap > ctx->big_cap) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->big_e);
+    cudaFree(ctx->big_off);
+    ctx->big_e = nullptr;
+    ctx->big_off = nullptr;
+    ctx->big_cap = 0;
+    cudaError_t e = alloc_big(bcap, &ctx->big_e, &ctx->big_off);
+    if (e != cudaSuccess) return cuda_fail(e, "big-list allocation");
+    ctx->big_cap = bcap;
+  }
   uint32_t cap = ctx->dbg_cap ? ctx->dbg_cap : std::max<uint32_t>(n, 1);
   if (cap > ctx->ws_cap || ctx->dbg_cap) {
     if (ctx->ws_items[0] || ctx->ws_items[1]) {
@@ -203,6 +227,10 @@ KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tu
   p.timeout_ns = ctx->dbg_timeout_us ? ctx->dbg_timeout_us * 1000ull : 2000000000ull;
   p.skip_cta = -1;
   p.init_state = 1;
+  p.trace = ctx->trace;
+  p.trace_cap = ctx->trace_cap;
+  p.big = (t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{ctx->big_e, ctx->big_off, ctx->big_cap};
+  if (ctx->dbg_big_cap && p.big.cap > ctx->dbg_big_cap) p.big.cap = ctx->dbg_big_cap;
   return p;
 }
 
@@ -264,6 +292,9 @@ irgl_status irgl_ctx_destroy(irgl_ctx* ctx) {
   cudaFree(ctx->ws_items[1]);
   cudaFree(ctx->ws_stamp);
   cudaFree(ctx->ws_state);
+  cudaFree(ctx->trace);
+  cudaFree(ctx->big_e);
+  cudaFree(ctx->big_off);
   cudaFree(ctx->st);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
   delete ctx;
@@ -285,12 +316,50 @@ irgl_status irgl_ctx_info(irgl_ctx* ctx, uint32_t* sm_count, irgl_tuning* defaul
   return IRGL_OK;
 }
 
+irgl_status irgl_trace_enable(irgl_ctx* ctx, uint32_t max_rounds) {
+  if (!ctx) return fail(IRGL_ERR_INVALID_ARG, "ctx is NULL");
+  DeviceGuard guard(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->trace);
+  ctx->trace = nullptr;
+  ctx->trace_cap = 0;
+  if (max_rounds == 0) return IRGL_OK;
+  const size_t bytes = sizeof(unsigned long long) * 2 * ((size_t)max_rounds + 1);
+  cudaError_t e = cudaMalloc(&ctx->trace, bytes);
+  if (e == cudaSuccess) e = cudaMemset(ctx->trace, 0, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "trace allocation");
+  ctx->trace_cap = max_rounds + 1;
+  return IRGL_OK;
+}
+
+irgl_status irgl_trace_read(irgl_ctx* ctx, uint64_t* t_ns, uint32_t* in_n, uint32_t* out_n, uint32_t cap,
+                            uint32_t* nrec) {
+  if (!ctx || !nrec) return fail(IRGL_ERR_INVALID_ARG, "NULL argument");
+  *nrec = 0;
+  if (!ctx->trace) return IRGL_OK;
+  DeviceGuard guard(ctx->device);
+  const uint32_t k = std::min(std::min(cap, ctx->trace_cap), ctx->st_host->rounds + 1);
+  std::vector<unsigned long long> buf(2 * (size_t)k);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess && k)
+    e = cudaMemcpy(buf.data(), ctx->trace, sizeof(unsigned long long) * buf.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "trace read");
+  for (uint32_t i = 0; i < k; ++i) {
+    if (t_ns) t_ns[i] = buf[2 * i];
+    if (in_n) in_n[i] = static_cast<uint32_t>(buf[2 * i + 1] >> 32);
+    if (out_n) out_n[i] = static_cast<uint32_t>(buf[2 * i + 1]);
+  }
+  *nrec = k;
+  return IRGL_OK;
+}
+
 irgl_status irgl_debug_set(irgl_ctx* ctx, int key, int64_t value) {
   if (!ctx) return fail(IRGL_ERR_INVALID_ARG, "ctx is NULL");
   switch (key) {
     case 1: ctx->dbg_timeout_us = value > 0 ? static_cast<uint64_t>(value) : 0; return IRGL_OK;
     case 2: ctx->dbg_skip_cta = static_cast<int>(value); return IRGL_OK;
     case 3: ctx->dbg_cap = value > 0 ? static_cast<uint32_t>(value) : 0; return IRGL_OK;
+    case 4: ctx->dbg_big_cap = value > 0 ? static_cast<uint32_t>(value) : 0; return IRGL_OK;
   }
   return fail(IRGL_ERR_INVALID_ARG, "unknown debug key %d", key);
 }

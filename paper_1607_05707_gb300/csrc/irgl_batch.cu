@@ -1,0 +1,473 @@
+// Batching: many independent queries (instances) in one persistent cooperative
+// launch, captured once in a CUDA graph and replayed.
+//
+// Layout: instance q owns arena[base_q, base_q + n_q) of the state arena and the
+// same range of the stamp arena; its worklist items are arena indices on the
+// shared double-buffered worklist; its termination flag is qlast[q], the round
+// of its last push. Bases are assigned in insertion order, so the descriptor
+// table is sorted by base and an item maps back to its instance by binary
+// search (the per-instance offset table).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "irgl.h"
+#include "irgl_internal.h"
+#include "irgl_launch.h"
+
+using namespace irgl;
+
+namespace {
+
+struct BQuery {
+  irgl_graph* g = nullptr;
+  uint32_t op = 0;
+  std::vector<uint32_t> srcs;
+  uint32_t base = 0;
+  uint32_t n = 0;
+  uint32_t rounds = 0;
+};
+
+}  // namespace
+
+struct irgl_batch {
+  irgl_ctx* ctx = nullptr;
+  uint32_t max_q = 0;
+  std::vector<BQuery> qs;
+  bool prepared = false;
+  uint64_t arena_n = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DevStatus* st = nullptr;
+  DevStatus* st_host = nullptr;
+  uint32_t* state = nullptr;
+  uint32_t* stamp = nullptr;
+  uint32_t* items[2] = {nullptr, nullptr};
+  uint32_t* qlast = nullptr;
+  uint32_t* qlast_host = nullptr;
+  uint32_t* cont = nullptr;
+  uint32_t* srcs = nullptr;
+  uint32_t* sbases = nullptr;
+  QDesc* desc = nullptr;
+  QNew* qnew = nullptr;
+  uint4* big_e = nullptr;
+  unsigned long long* big_off = nullptr;
+  uint32_t big_cap = 0;
+  irgl_tuning t{};
+  uint32_t grid = 0;
+  BParams bp{};
+  AdmitParams ap{};
+  uint32_t admit_grid = 0;
+  bool graph_ok = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace irgl {
+
+// Sec. 4.4: the control kernel's block size must lie in the intersection of
+// the block sizes every kernel of the outlined Pipe accepts; empty means no
+// outlining; with several candidates the highest is taken, unless the caller's
+// preferred size is in the set.
+irgl_status control_cta(const uint32_t* masks, uint32_t count, uint32_t preferred, uint32_t* out) {
+  uint32_t inter = 0xFu;  // bit i <=> CTA size 128 << i
+  for (uint32_t i = 0; i < count; ++i) inter &= masks[i];
+  if (inter == 0) return fail(IRGL_ERR_UNSUPPORTED, "no block size satisfies every kernel: outlining impossible");
+  if (preferred) {
+    for (uint32_t b = 0; b < 4; ++b)
+      if ((128u << b) == preferred && (inter >> b & 1u)) {
+        *out = preferred;
+        return IRGL_OK;
+      }
+  }
+  for (int b = 3; b >= 0; --b)
+    if (inter >> b & 1u) {
+      *out = 128u << b;
+      return IRGL_OK;
+    }
+  return fail(IRGL_ERR_UNSUPPORTED, "empty block-size set");
+}
+
+// Block sizes each kernel instance is compiled for (FixedBlock templates).
+uint32_t kernel_cta_mask(uint32_t op) {
+  (void)op;
+  return 0xFu;  // 128, 256, 512, 1024 for BFS, SSSP and CC alike
+}
+
+}  // namespace irgl
+
+namespace {
+
+void batch_free_device(irgl_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  cudaFree(b->state);
+  cudaFree(b->stamp);
+  cudaFree(b->items[0]);
+  cudaFree(b->items[1]);
+  cudaFree(b->qlast);
+  cudaFree(b->cont);
+  cudaFree(b->srcs);
+  cudaFree(b->sbases);
+  cudaFree(b->desc);
+  cudaFree(b->qnew);
+  cudaFree(b->big_e);
+  cudaFree(b->big_off);
+  b->big_e = nullptr;
+  b->big_off = nullptr;
+  b->big_cap = 0;
+  if (b->qlast_host) cudaFreeHost(b->qlast_host);
+  b->state = b->stamp = b->items[0] = b->items[1] = b->qlast = b->cont = b->srcs = b->sbases = nullptr;
+  b->qlast_host = nullptr;
+  b->desc = nullptr;
+  b->qnew = nullptr;
+  b->prepared = false;
+}
+
+void batch_reset_status(irgl_batch* b) {
+  DevStatus z;
+  std::memset(&z, 0, sizeof(z));
+  z.epoch = 1;
+  *b->st_host = z;
+  cudaMemcpyAsync(b->st, b->st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, b->stream);
+  if (b->stamp) cudaMemsetAsync(b->stamp, 0, sizeof(uint32_t) * b->arena_n, b->stream);
+  cudaStreamSynchronize(b->stream);
+}
+
+cudaError_t enqueue(irgl_batch* b) {
+  cudaError_t e = cudaMemsetAsync(b->cont, 0, 2 * sizeof(uint32_t), b->stream);
+  if (e == cudaSuccess) e = launch_admit(b->ap, b->admit_grid, b->stream);
+  if (e == cudaSuccess) e = launch_batch_iterate(b->t.cta_size, b->grid, b->bp, b->stream);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+irgl_status irgl_control_cta(const uint32_t* masks, uint32_t count, uint32_t preferred, uint32_t* out) {
+  if ((count && !masks) || !out) return fail(IRGL_ERR_INVALID_ARG, "NULL argument");
+  return control_cta(masks, count, preferred, out);
+}
+
+irgl_status irgl_batch_create(irgl_ctx* ctx, uint32_t max_queries, irgl_batch** out) {
+  if (!ctx || !out) return fail(IRGL_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (max_queries == 0 || max_queries > static_cast<uint32_t>(kMaxBatchQueries))
+    return fail(IRGL_ERR_INVALID_ARG, "max_queries must be in 1..%d", kMaxBatchQueries);
+  DeviceGuard guard(ctx->device);
+  irgl_batch* b = new (std::nothrow) irgl_batch();
+  if (!b) return fail(IRGL_ERR_OOM, "batch allocation");
+  b->ctx = ctx;
+  b->max_q = max_queries;
+  b->stream = ctx->stream;
+  cudaError_t e = cudaSuccess;
+  if (!b->stream) {  // the legacy default stream cannot be captured: use a private one
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    b->own_stream = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->st, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->st_host, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
+  if (e != cudaSuccess) {
+    irgl_batch_destroy(b);
+    return cuda_fail(e, "batch setup");
+  }
+  batch_reset_status(b);
+  *out = b;
+  return IRGL_OK;
+}
+
+irgl_status irgl_batch_destroy(irgl_batch* b) {
+  if (!b) return IRGL_OK;
+  DeviceGuard guard(b->ctx->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_free_device(b);
+  cudaFree(b->st);
+  if (b->st_host) cudaFreeHost(b->st_host);
+  if (b->ev[0]) cudaEventDestroy(b->ev[0]);
+  if (b->ev[1]) cudaEventDestroy(b->ev[1]);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return IRGL_OK;
+}
+
+irgl_status irgl_batch_add(irgl_batch* b, irgl_graph* g, irgl_kernel k, const uint32_t* srcs_host, uint32_t nsrc,
+                           uint32_t* query_id) {
+  if (!b || !g || (nsrc && !srcs_host)) return fail(IRGL_ERR_INVALID_ARG, "NULL argument");
+  if (b->prepared) return fail(IRGL_ERR_INVALID_ARG, "batch already prepared");
+  if (b->qs.size() >= b->max_q) return fail(IRGL_ERR_INVALID_ARG, "batch is full (%u queries)", b->max_q);
+  if (g->ctx != b->ctx) return fail(IRGL_ERR_INVALID_ARG, "graph belongs to another context");
+  irgl_status s = check_kernel_graph(k, g);
+  if (s != IRGL_OK) return s;
+  if (k != IRGL_CC && nsrc == 0) return fail(IRGL_ERR_INVALID_ARG, "BFS/SSSP need at least one source");
+  for (uint32_t i = 0; i < nsrc; ++i)
+    if (srcs_host[i] >= g->n) return fail(IRGL_ERR_INVALID_ARG, "source %u out of range", srcs_host[i]);
+  BQuery q;
+  q.g = g;
+  q.op = static_cast<uint32_t>(k);
+  q.n = g->n;
+  if (k != IRGL_CC) q.srcs.assign(srcs_host, srcs_host + nsrc);
+  if (query_id) *query_id = static_cast<uint32_t>(b->qs.size());
+  b->qs.push_back(std::move(q));
+  return IRGL_OK;
+}
+
+irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cuda_graph) {
+  if (!b) return fail(IRGL_ERR_INVALID_ARG, "batch is NULL");
+  if (b->qs.empty()) return fail(IRGL_ERR_INVALID_ARG, "batch has no queries");
+  DeviceGuard guard(b->ctx->device);
+  irgl_ctx* ctx = b->ctx;
+  irgl_tuning t;
+  irgl_status s = resolve_tuning(tin, &t);
+  if (s != IRGL_OK) return s;
+  // T_control: one CTA size valid for every kernel hosted by the launch
+  std::vector<uint32_t> masks;
+  for (auto& q : b->qs) masks.push_back(kernel_cta_mask(q.op));
+  uint32_t cta = 0;
+  s = control_cta(masks.data(), static_cast<uint32_t>(masks.size()), tin && tin->cta_size ? t.cta_size : 0, &cta);
+  if (s != IRGL_OK) return s;
+  t.cta_size = cta;
+  if (b->prepared) {
+    cudaStreamSynchronize(b->stream);
+    batch_free_device(b);
+  }
+  // arena
+  uint64_t total = 0, nsrc = 0;
+  for (auto& q : b->qs) {
+    q.base = static_cast<uint32_t>(total);
+    total += q.n;
+    nsrc += q.srcs.size();
+    if (total >= 0xFFFFFFFFull) return fail(IRGL_ERR_INVALID_ARG, "batch arena exceeds 2^32 - 1 entries");
+  }
+  b->arena_n = std::max<uint64_t>(total, 1);
+  const uint32_t Q = static_cast<uint32_t>(b->qs.size());
+  std::vector<QDesc> desc(Q);
+  std::vector<QNew> qn(Q);
+  std::vector<uint32_t> bases(Q), flat;
+  flat.reserve(nsrc);
+  for (uint32_t i = 0; i < Q; ++i) {
+    const BQuery& q = b->qs[i];
+    desc[i] = QDesc{q.g->row_ptr, q.g->col, q.g->w, q.n, q.op, q.base, i};
+    bases[i] = q.base;
+    qn[i] = QNew{q.base, q.n, q.op, i, static_cast<uint32_t>(flat.size()), static_cast<uint32_t>(q.srcs.size()),
+                 q.base, 0};
+    flat.insert(flat.end(), q.srcs.begin(), q.srcs.end());
+  }
+  cudaError_t e = cudaMalloc(&b->state, sizeof(uint32_t) * b->arena_n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->stamp, sizeof(uint32_t) * b->arena_n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->items[0], sizeof(uint32_t) * b->arena_n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->items[1], sizeof(uint32_t) * b->arena_n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->qlast, sizeof(uint32_t) * Q);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->qlast_host, sizeof(uint32_t) * Q);
+  if (e == cudaSuccess) e = cudaMalloc(&b->cont, 128);
+  if (e == cudaSuccess) e = cudaMalloc(&b->srcs, sizeof(uint32_t) * std::max<size_t>(flat.size(), 1));
+  if (e == cudaSuccess) e = cudaMalloc(&b->sbases, sizeof(uint32_t) * Q);
+  if (e == cudaSuccess) e = cudaMalloc(&b->desc, sizeof(QDesc) * Q);
+  if (e == cudaSuccess) e = cudaMalloc(&b->qnew, sizeof(QNew) * Q);
+  if (e == cudaSuccess) {
+    b->big_cap = big_capacity(b->arena_n);
+    e = alloc_big(b->big_cap, &b->big_e, &b->big_off);
+  }
+  if (e != cudaSuccess) {
+    batch_free_device(b);
+    return cuda_fail(e, "batch arena allocation");
+  }
+  e = cudaMemsetAsync(b->stamp, 0, sizeof(uint32_t) * b->arena_n, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->cont, 0, 128, b->stream);
+  if (e == cudaSuccess && !flat.empty())
+    e = cudaMemcpyAsync(b->srcs, flat.data(), sizeof(uint32_t) * flat.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->sbases, bases.data(), sizeof(uint32_t) * Q, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->desc, desc.data(), sizeof(QDesc) * Q, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->qnew, qn.data(), sizeof(QNew) * Q, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    batch_free_device(b);
+    return cuda_fail(e, "batch upload");
+  }
+  // persistent grid
+  int nb = 0;
+  e = occupancy_batch(t.cta_size, &nb);
+  if (e != cudaSuccess || nb <= 0) {
+    batch_free_device(b);
+    return fail(IRGL_ERR_CUDA, "batched kernel cannot be made resident");
+  }
+  if (t.blocks_per_sm && static_cast<int>(t.blocks_per_sm) < nb) nb = static_cast<int>(t.blocks_per_sm);
+  b->grid = static_cast<uint32_t>(nb) * static_cast<uint32_t>(ctx->sm_count);
+  if (t.max_blocks && t.max_blocks < b->grid) b->grid = t.max_blocks;
+  b->t = t;
+  b->bp = BParams{};
+  b->bp.desc = b->desc;
+  b->bp.sbases = b->sbases;
+  b->bp.nq = Q;
+  b->bp.state = b->state;
+  b->bp.stamp = b->stamp;
+  b->bp.qlast = b->qlast;
+  b->bp.items[0] = b->items[0];
+  b->bp.items[1] = b->items[1];
+  b->bp.cap = static_cast<uint32_t>(b->arena_n);
+  b->bp.cont = b->cont;
+  b->bp.st = b->st;
+  b->bp.tn = Tune{t.warp_thresh, t.cta_thresh, t.chunk};
+  b->bp.max_rounds = 0xFFFFFFFFu;
+  b->bp.rounds_cap_is_error = 1;
+  b->bp.timeout_ns = ctx->dbg_timeout_us ? ctx->dbg_timeout_us * 1000ull : 2000000000ull;
+  b->bp.trace = ctx->trace;
+  b->bp.trace_cap = ctx->trace_cap;
+  b->bp.big = (t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{b->big_e, b->big_off, b->big_cap};
+  b->ap = AdmitParams{};
+  b->ap.qn = b->qnew;
+  b->ap.nnew = Q;
+  b->ap.total = static_cast<uint32_t>(total);
+  b->ap.srcs = b->srcs;
+  b->ap.state = b->state;
+  b->ap.qlast = b->qlast;
+  b->ap.items[0] = b->items[0];
+  b->ap.items[1] = b->items[1];
+  b->ap.cap = static_cast<uint32_t>(b->arena_n);
+  b->ap.cont = b->cont;
+  b->ap.st = b->st;
+  b->admit_grid = static_cast<uint32_t>(ctx->sm_count) * 4;
+  b->graph_ok = false;
+  if (use_cuda_graph) {
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue(b);
+      cudaGraph_t gr = nullptr;
+      e = cudaStreamEndCapture(b->stream, &gr);
+      if (e2 == cudaSuccess && e == cudaSuccess && gr) {
+        e = cudaGraphInstantiate(&b->exec, gr, 0);
+        if (e == cudaSuccess) {
+          b->graph = gr;
+          b->graph_ok = true;
+        } else {
+          cudaGraphDestroy(gr);
+        }
+      } else if (gr) {
+        cudaGraphDestroy(gr);
+      }
+    }
+    cudaGetLastError();  // a failed capture falls back to direct launches
+  }
+  b->prepared = true;
+  return IRGL_OK;
+}
+
+irgl_status irgl_batch_launch(irgl_batch* b) {
+  if (!b || !b->prepared) return fail(IRGL_ERR_INVALID_ARG, "batch not prepared");
+  DeviceGuard guard(b->ctx->device);
+  cudaError_t e = cudaEventRecord(b->ev[0], b->stream);
+  if (e == cudaSuccess) e = b->graph_ok ? cudaGraphLaunch(b->exec, b->stream) : enqueue(b);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev[1], b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  return IRGL_OK;
+}
+
+irgl_status irgl_batch_sync(irgl_batch* b, irgl_stats* stats) {
+  if (!b || !b->prepared) return fail(IRGL_ERR_INVALID_ARG, "batch not prepared");
+  DeviceGuard guard(b->ctx->device);
+  const uint32_t Q = static_cast<uint32_t>(b->qs.size());
+  cudaError_t e = cudaMemcpyAsync(b->st_host, b->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->qlast_host, b->qlast, sizeof(uint32_t) * Q, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+  const DevStatus st = *b->st_host;
+  b->ctx->st_host->rounds = st.rounds;  // lets irgl_trace_read size a batch trace
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->rounds = st.rounds;
+    stats->grid = b->grid;
+    stats->cta_size = b->t.cta_size;
+    stats->launches = 3;
+    stats->edges_scanned = st.edges;
+    stats->last_out = st.last_out;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess) stats->device_ms = ms;
+  }
+  if (st.err != DERR_NONE) {
+    irgl_status s = IRGL_ERR_CUDA;
+    switch (st.err) {
+      case DERR_WL_OVERFLOW: s = fail(IRGL_ERR_WL_OVERFLOW, "a push found the batch worklist full"); break;
+      case DERR_BARRIER_TIMEOUT: s = fail(IRGL_ERR_BARRIER_TIMEOUT, "grid barrier wait exceeded its time limit"); break;
+      case DERR_MAX_ROUNDS: s = fail(IRGL_ERR_MAX_ROUNDS, "batch reached max_rounds with work left"); break;
+      case DERR_BAD_ITEM: s = fail(IRGL_ERR_INVALID_ARG, "a worklist item is not a vertex of its graph"); break;
+      default: s = fail(IRGL_ERR_CUDA, "unknown device error %u", st.err); break;
+    }
+    batch_reset_status(b);
+    return s;
+  }
+  // per-instance rounds from the termination flags
+  const uint32_t ep0 = st.epoch - st.rounds;  // round id of this run's first round
+  for (uint32_t i = 0; i < Q; ++i) b->qs[i].rounds = b->qlast_host[i] - ep0 + 2;
+  cudaMemsetAsync(&b->st->edges, 0, sizeof(unsigned long long), b->stream);
+  if (st.epoch > 0xF0000000u) batch_reset_status(b);
+  return IRGL_OK;
+}
+
+irgl_status irgl_batch_run(irgl_batch* b, irgl_stats* stats) {
+  irgl_status s = irgl_batch_launch(b);
+  if (s != IRGL_OK) return s;
+  return irgl_batch_sync(b, stats);
+}
+
+irgl_status irgl_batch_autotune(irgl_batch* b, uint32_t reps, irgl_tuning* best, float* best_ms) {
+  if (!b || !b->prepared || !best) return fail(IRGL_ERR_INVALID_ARG, "NULL argument or batch not prepared");
+  const int use_graph = b->graph_ok ? 1 : 0;
+  reps = std::max<uint32_t>(reps, 1);
+  auto measure = [&](const irgl_tuning& t) -> float {
+    if (irgl_batch_prepare(b, &t, use_graph) != IRGL_OK) return -1.f;
+    std::vector<float> ms;
+    for (uint32_t r = 0; r <= reps; ++r) {
+      irgl_stats st;
+      if (irgl_batch_run(b, &st) != IRGL_OK) return -1.f;
+      if (r) ms.push_back(st.device_ms);
+    }
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+  };
+  irgl_status s = tune_descend(measure, best, best_ms);
+  if (s == IRGL_OK) s = irgl_batch_prepare(b, best, use_graph);
+  return s;
+}
+
+irgl_status irgl_batch_info(irgl_batch* b, uint32_t* nqueries, uint32_t* grid, uint32_t* cta_size,
+                            int* graph_captured, uint64_t* arena_entries) {
+  if (!b) return fail(IRGL_ERR_INVALID_ARG, "batch is NULL");
+  if (nqueries) *nqueries = static_cast<uint32_t>(b->qs.size());
+  if (grid) *grid = b->grid;
+  if (cta_size) *cta_size = b->t.cta_size;
+  if (graph_captured) *graph_captured = b->graph_ok ? 1 : 0;
+  if (arena_entries) *arena_entries = b->arena_n;
+  return IRGL_OK;
+}
+
+irgl_status irgl_batch_result(irgl_batch* b, uint32_t query_id, uint32_t** state_dev, uint32_t* n, uint32_t* rounds) {
+  if (!b || !b->prepared) return fail(IRGL_ERR_INVALID_ARG, "batch not prepared");
+  if (query_id >= b->qs.size()) return fail(IRGL_ERR_INVALID_ARG, "query id out of range");
+  const BQuery& q = b->qs[query_id];
+  if (state_dev) *state_dev = b->state + q.base;
+  if (n) *n = q.n;
+  if (rounds) *rounds = q.rounds;
+  return IRGL_OK;
+}
+
+irgl_status irgl_batch_copy_result(irgl_batch* b, uint32_t query_id, uint32_t* host_out) {
+  if (!b || !b->prepared || !host_out) return fail(IRGL_ERR_INVALID_ARG, "NULL argument or batch not prepared");
+  if (query_id >= b->qs.size()) return fail(IRGL_ERR_INVALID_ARG, "query id out of range");
+  DeviceGuard guard(b->ctx->device);
+  const BQuery& q = b->qs[query_id];
+  cudaError_t e = cudaMemcpyAsync(host_out, b->state + q.base, sizeof(uint32_t) * (size_t)q.n,
+                                  cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch result copy");
+  return IRGL_OK;
+}
+
+}  // extern "C"

@@ -45,13 +45,15 @@ enum : uint32_t {
 };
 
 // Device status block. Each contended family sits on its own 128-byte line.
-// Invariant between launches: bar_count, exit_count, tail[], grab[],
-// any_true and any_false are 0 (every kernel restores them on a clean exit;
-// the host clears the block after an error).
+// Invariant between launches: arrive, exit_count, tail[], grab[], rel,
+// big_ctr, any_true and any_false are 0 (every kernel restores them on a
+// clean exit; the host clears the block after an error).
 struct alignas(128) DevStatus {
-  uint32_t bar_count;
+  // grid-barrier arrivals of the current barrier: (pushes << 32) | (CTAs that
+  // appended to the big list << 16) | arrivals; reset by each barrier's releaser
+  unsigned long long arrive;
   uint32_t exit_count;
-  uint32_t pad0[30];
+  uint32_t pad0[29];
   uint32_t tail[4];
   uint32_t pad1[28];
   uint32_t grab[4];
@@ -66,8 +68,27 @@ struct alignas(128) DevStatus {
   uint32_t last_out;  // out-worklist size when a persistent launch stopped
   unsigned long long edges;  // adjacency entries scanned (accumulates until the host clears it)
   uint32_t pad3[22];
+  // grid-barrier release word: (generation << 40) | (flags << 32) | published out-worklist size,
+  // flags = device error code (bits 0..6) | big-list-pending (bit 7)
+  unsigned long long rel;
+  uint32_t pad4[30];
+  // big list of the current round: (entries << 40) | edges, appended with one atomic per tile
+  unsigned long long big_ctr;
+  unsigned long long big_pub;  // copy published by the barrier's releaser
+  uint32_t pad5[28];
 };
-static_assert(sizeof(DevStatus) == 512, "status layout");
+static_assert(sizeof(DevStatus) == 768, "status layout");
+
+// Long adjacency lists of a round (degree >= cta_thresh) are not walked by the
+// CTA that popped them: they go to a grid-wide list and, after a barrier, every
+// CTA walks an equal share of their concatenated edges.
+struct BigList {
+  uint4* e;                  // {beg, end, val, q}
+  unsigned long long* off;   // first edge of each entry in the concatenation (increasing)
+  uint32_t cap;              // entries; 0 = disabled (lists stay in the CTA bin)
+};
+constexpr unsigned long long kBigEdgeMask = (1ull << 40) - 1;
+constexpr uint32_t kRelBigFlag = 0x80u;
 
 // __launch_bounds__ minimum CTAs per SM: 1024 resident threads per SM, so the
 // register allocator may use up to 64 registers per thread.
@@ -102,6 +123,9 @@ struct KParams {
   unsigned long long timeout_ns;
   int skip_cta;                // test hook: this CTA never reaches the first barrier
   int init_state;              // write the Iterate initial values in the prologue
+  unsigned long long* trace;   // optional per-round trace: {end time ns, (in_n << 32) | out_n}
+  uint32_t trace_cap;          // rounds the trace can hold
+  BigList big;
 };
 
 // Per-launch (one round) arguments.
@@ -114,6 +138,41 @@ struct RoundArgs {
   uint32_t* out_tail;
   uint32_t out_cap;
   uint32_t level;            // BFS LEVEL
+};
+
+// Batched mode: one descriptor per query (instance), kept sorted by arena base.
+// A worklist item is an arena index base + v; its query is found by binary
+// search over the sorted bases (the per-instance offset table).
+constexpr int kMaxBatchQueries = 1024;
+
+struct QDesc {
+  const uint32_t* row_ptr;
+  const uint32_t* col;
+  const int32_t* w;
+  uint32_t n;     // vertices of the query's graph
+  uint32_t op;    // OP_BFS / OP_SSSP / OP_CC
+  uint32_t base;  // arena offset of the query's state (and stamps)
+  uint32_t slot;  // query id (index into qlast)
+};
+
+struct BParams {
+  const QDesc* desc;        // nq descriptors, sorted by base
+  const uint32_t* sbases;   // nq sorted bases
+  uint32_t nq;
+  uint32_t* state;          // arena: state of every query
+  uint32_t* stamp;          // arena: push dedup stamps
+  uint32_t* qlast;          // per query id: stamp (round id) of its last push
+  uint32_t* items[2];       // shared worklists of arena indices
+  uint32_t cap;
+  uint32_t* cont;           // cont[0]: buffer holding pending items, cont[1]: their count
+  DevStatus* st;
+  Tune tn;
+  uint32_t max_rounds;      // rounds per launch (an epoch); 0xFFFFFFFF = run to empty
+  int rounds_cap_is_error;  // 1: hitting max_rounds is DERR_MAX_ROUNDS; 0: epoch end
+  unsigned long long timeout_ns;
+  unsigned long long* trace;
+  uint32_t trace_cap;
+  BigList big;
 };
 
 // ----------------------------------------------------------------------------- small helpers
@@ -173,8 +232,25 @@ struct Smem {
   uint32_t flag;
   uint32_t own_tid, own_beg, own_end, own_val, own_q;
   uint32_t red;
+  uint32_t pub_out;  // out-worklist size published by the grid barrier
+  uint32_t pub_err;  // device error code published by the grid barrier
+  uint32_t round_pushes;                    // out-worklist slots this CTA reserved in the current round
+  uint32_t big_appended;                    // this CTA appended to the big list in the current round
+  uint32_t pub_flags;                       // kRelBigFlag when the big list is pending
+  unsigned long long pub_big;               // published big-list counter
+  unsigned long long big_base;              // this tile's reservation in the big list
+  unsigned long long warp_big[kWarps + 1];
+  static constexpr int kBigWin = 256;       // big-list window held in shared memory
+  uint4 be[kBigWin];                        // entries {beg, end, val, q}
+  unsigned long long bo[kBigWin];           // their first edge in the concatenation
   unsigned long long edges;
   uint8_t pushed[CTA];   // ReduceAndReturn All: item pushed something
+};
+
+template <int CTA>
+struct BatchSmem {
+  Smem<CTA> core;
+  uint32_t sbases[kMaxBatchQueries];
 };
 
 // ----------------------------------------------------------------------------- cooperative-conversion push
@@ -185,7 +261,10 @@ template <int CTA>
 __device__ __forceinline__ void flush_stage(Smem<CTA>& sm, const Out& out) {
   const uint32_t n = min(sm.stage_n, static_cast<uint32_t>(Smem<CTA>::kStage));
   if (n == 0) return;
-  if (threadIdx.x == 0) sm.gbase = atomicAdd(out.tail, n);
+  if (threadIdx.x == 0) {
+    sm.gbase = atomicAdd(out.tail, n);
+    sm.round_pushes += n;
+  }
   __syncthreads();
   const uint32_t gb = sm.gbase;
   for (uint32_t i = threadIdx.x; i < n; i += CTA) {
@@ -199,15 +278,17 @@ __device__ __forceinline__ void flush_stage(Smem<CTA>& sm, const Out& out) {
 }
 
 // Items that did not fit the stage go straight to global memory, aggregated per warp.
-__device__ __forceinline__ void push_global_warp(const Out& out, uint32_t cnt_lane, uint32_t incl_unused,
+__device__ __forceinline__ void push_global_warp(const Out& out, uint32_t* round_pushes, uint32_t cnt_lane,
                                                  uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
-  (void)incl_unused;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t incl = warp_incl_scan(cnt_lane);
   const uint32_t total = __shfl_sync(kFull, incl, 31);
   if (total == 0) return;
   uint32_t gb = 0;
-  if (lane == 31) gb = atomicAdd(out.tail, total);
+  if (lane == 31) {
+    gb = atomicAdd(out.tail, total);
+    atomicAdd(round_pushes, total);
+  }
   gb = __shfl_sync(kFull, gb, 31);
   uint32_t pos = gb + incl - cnt_lane;
   const uint32_t vs[4] = {v0, v1, v2, v3};
@@ -237,7 +318,7 @@ __device__ __forceinline__ void push1(Smem<CTA>& sm, const Out& out, bool p, uin
   if (p && fits) sm.stage[pos] = v;
   if (base + cnt > static_cast<uint32_t>(Smem<CTA>::kStage)) {
     const bool ov = p && !fits;
-    push_global_warp(out, ov ? 1u : 0u, 0u, v, 0u, 0u, 0u);
+    push_global_warp(out, &sm.round_pushes, ov ? 1u : 0u, v, 0u, 0u, 0u);
   }
 }
 
@@ -281,7 +362,7 @@ __device__ __forceinline__ void push4(Smem<CTA>& sm, const Out& out, uint32_t f,
       const uint32_t val = src == 0 ? o[0] : src == 1 ? o[1] : src == 2 ? o[2] : o[3];
       if (i == 0) g0 = val; else if (i == 1) g1 = val; else if (i == 2) g2 = val; else g3 = val;
     }
-    push_global_warp(out, ov, 0u, g0, g1, g2, g3);
+    push_global_warp(out, &sm.round_pushes, ov, g0, g1, g2, g3);
   }
 }
 
@@ -305,6 +386,35 @@ __device__ __forceinline__ uint32_t cta_excl_scan(Smem<CTA>& sm, uint32_t x, uin
   return sm.warp_sums[wid] + incl - x;
 }
 
+template <int CTA>
+__device__ __forceinline__ unsigned long long cta_excl_scan64(Smem<CTA>& sm, unsigned long long x,
+                                                            unsigned long long& total) {
+  constexpr int NW = Smem<CTA>::kWarps;
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= static_cast<uint32_t>(o)) incl += t;
+  }
+  if (lane == 31) sm.warp_big[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned long long v = lane < static_cast<uint32_t>(NW) ? sm.warp_big[lane] : 0ull;
+    unsigned long long vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(kFull, vi, o);
+      if (lane >= static_cast<uint32_t>(o)) vi += t;
+    }
+    if (lane < static_cast<uint32_t>(NW)) sm.warp_big[lane] = vi - v;
+    if (lane == static_cast<uint32_t>(NW) - 1) sm.warp_big[NW] = vi;
+  }
+  __syncthreads();
+  total = sm.warp_big[NW];
+  return sm.warp_big[wid] + incl - x;
+}
+
 // ----------------------------------------------------------------------------- graph views
 
 // One graph, vertex ids are state indices. OP fixed at compile time.
@@ -324,6 +434,41 @@ struct SingleView {
   __device__ __forceinline__ const int32_t* wp(uint32_t) const { return w; }
   __device__ __forceinline__ uint32_t sbase(uint32_t) const { return 0u; }
   __device__ __forceinline__ void decode(uint32_t item, uint32_t& q, uint32_t& u) const { q = 0; u = item; }
+  __device__ __forceinline__ void mark(uint32_t, uint32_t) const {}
+};
+
+// Many queries over many graphs; op taken per query at run time.
+struct BatchView {
+  const QDesc* __restrict__ desc;
+  const uint32_t* sbases;  // shared-memory copy
+  uint32_t nq;
+  uint32_t* state;
+  uint32_t* stamp;
+  uint32_t* qlast;
+  static constexpr bool kBatched = true;
+  __device__ __forceinline__ uint32_t op(uint32_t q) const { return __ldg(&desc[q].op); }
+  __device__ __forceinline__ const uint32_t* rowp(uint32_t q) const {
+    return reinterpret_cast<const uint32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&desc[q].row_ptr)));
+  }
+  __device__ __forceinline__ const uint32_t* colp(uint32_t q) const {
+    return reinterpret_cast<const uint32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&desc[q].col)));
+  }
+  __device__ __forceinline__ const int32_t* wp(uint32_t q) const {
+    return reinterpret_cast<const int32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&desc[q].w)));
+  }
+  __device__ __forceinline__ uint32_t sbase(uint32_t q) const { return sbases[q]; }
+  __device__ __forceinline__ uint32_t nverts(uint32_t q) const { return __ldg(&desc[q].n); }
+  __device__ __forceinline__ void decode(uint32_t item, uint32_t& q, uint32_t& u) const {
+    uint32_t lo = 0, hi = nq - 1;
+    while (lo < hi) {
+      const uint32_t md = (lo + hi + 1) >> 1;
+      if (sbases[md] <= item) lo = md;
+      else hi = md - 1;
+    }
+    q = lo;
+    u = item - sbases[lo];
+  }
+  __device__ __forceinline__ void mark(uint32_t q, uint32_t ep) const { qlast[__ldg(&desc[q].slot)] = ep; }
 };
 
 // ----------------------------------------------------------------------------- operator
@@ -342,6 +487,23 @@ __device__ __forceinline__ bool relax(uint32_t op_rt, uint32_t* state, uint32_t*
   }
   const uint32_t nd = op == OP_SSSP ? val + static_cast<uint32_t>(wt) : val;
   if (nd >= __ldcg(state + v)) return false;
+  const uint32_t old = atomicMin(state + v, nd);
+  if (nd >= old) return false;
+  return atomicExch(stamp + v, ep) != ep;
+}
+
+// Same operator with the destination's current value `cur` already loaded, so
+// callers can issue all their state loads before the first atomic.
+template <uint32_t OP>
+__device__ __forceinline__ bool decide(uint32_t op_rt, uint32_t* state, uint32_t* stamp, uint32_t v, uint32_t val,
+                                       int32_t wt, uint32_t cur, uint32_t ep) {
+  const uint32_t op = OP == OP_RUNTIME ? op_rt : OP;
+  if (op == OP_BFS) {
+    if (cur != kInf) return false;
+    return atomicCAS(state + v, kInf, val) == kInf;
+  }
+  const uint32_t nd = op == OP_SSSP ? val + static_cast<uint32_t>(wt) : val;
+  if (nd >= cur) return false;
   const uint32_t old = atomicMin(state + v, nd);
   if (nd >= old) return false;
   return atomicExch(stamp + v, ep) != ep;
@@ -388,10 +550,13 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Out
       c = __ldg(reinterpret_cast<const uint4*>(col + e));
       int4 ww = make_int4(0, 0, 0, 0);
       if (nw) ww = __ldg(reinterpret_cast<const int4*>(w + e));
-      f |= relax<OP>(op, state, stamp, c.x, val, ww.x, ep) ? 1u : 0u;
-      f |= relax<OP>(op, state, stamp, c.y, val, ww.y, ep) ? 2u : 0u;
-      f |= relax<OP>(op, state, stamp, c.z, val, ww.z, ep) ? 4u : 0u;
-      f |= relax<OP>(op, state, stamp, c.w, val, ww.w, ep) ? 8u : 0u;
+      // all four destination loads in flight before any atomic
+      const uint32_t c0 = __ldcg(state + c.x), c1 = __ldcg(state + c.y);
+      const uint32_t c2 = __ldcg(state + c.z), c3 = __ldcg(state + c.w);
+      f |= decide<OP>(op, state, stamp, c.x, val, ww.x, c0, ep) ? 1u : 0u;
+      f |= decide<OP>(op, state, stamp, c.y, val, ww.y, c1, ep) ? 2u : 0u;
+      f |= decide<OP>(op, state, stamp, c.z, val, ww.z, c2, ep) ? 4u : 0u;
+      f |= decide<OP>(op, state, stamp, c.w, val, ww.w, c3, ep) ? 8u : 0u;
     }
     push4<CTA>(sm, out, f, sb + c.x, sb + c.y, sb + c.z, sb + c.w);
     any |= f != 0;
@@ -411,6 +576,7 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Out
     push1<CTA>(sm, out, p, sb + v);
     any |= p;
   }
+  if (V::kBatched && any) g.mark(q, ep);  // per-instance termination flag: last round with a push
   return any;
 }
 
@@ -424,6 +590,8 @@ struct RoundCtx {
   uint32_t ep;       // dedup stamp of this round
   uint32_t* grab;
   Tune tn;
+  BigList big;                    // cap 0: long lists stay in the CTA bin
+  unsigned long long* big_ctr;
 };
 
 template <uint32_t OP, int CTA, int RED, class V>
@@ -453,8 +621,38 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
   edges += deg;
   bool pushed = false;
 
+  // Long lists: with the big list enabled they are appended (one atomic per
+  // tile reserves slots and edge offsets together) and walked by the whole grid
+  // after the round's first barrier; otherwise (or when the list is full) the
+  // CTA bin below walks them.
+  // With the big list on, a frontier smaller than one tile per CTA sends every
+  // list of warp size or more to the grid phase (the few CTAs holding items
+  // would otherwise walk them alone); larger frontiers send lists >= cta_thresh.
+  const uint32_t split = (rc.big.cap != 0 && rc.in_n < gridDim.x * CTA) ? min(rc.tn.warp_thresh, rc.tn.cta_thresh)
+                                                                         : rc.tn.cta_thresh;
+  bool big = deg >= split;
+  if (rc.big.cap != 0 && __syncthreads_or(big)) {
+    const unsigned long long mine = big ? ((1ull << 40) | deg) : 0ull;
+    unsigned long long total = 0;
+    const unsigned long long ex = cta_excl_scan64<CTA>(sm, mine, total);
+    if (total != 0) {
+      if (tid == 0) {
+        sm.big_base = atomicAdd(rc.big_ctr, total);
+        sm.big_appended = 1;
+      }
+      __syncthreads();
+      if (big) {
+        const unsigned long long at = sm.big_base + ex;
+        const uint32_t slot = static_cast<uint32_t>(at >> 40);
+        if (slot < rc.big.cap) {
+          rc.big.e[slot] = make_uint4(beg, end, val, q);
+          rc.big.off[slot] = at & kBigEdgeMask;
+          big = false;
+        }
+      }
+    }
+  }
   // CTA bin: the whole CTA walks one long list at a time.
-  bool big = deg >= rc.tn.cta_thresh;
   while (__syncthreads_or(big)) {
     if (big) sm.own_tid = tid;
     __syncthreads();
@@ -472,7 +670,7 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
   }
 
   // Warp bin: each warp walks its members' medium lists one at a time.
-  bool mid = valid && deg >= rc.tn.warp_thresh && deg < rc.tn.cta_thresh;
+  bool mid = valid && deg >= rc.tn.warp_thresh && deg < split;
   for (;;) {
     const unsigned m = __ballot_sync(kFull, mid);
     if (m == 0) break;
@@ -488,7 +686,7 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
   }
 
   // Scan bin: short lists of the whole tile, one edge per thread per strip.
-  const bool small = valid && deg > 0 && deg < rc.tn.warp_thresh && deg < rc.tn.cta_thresh;
+  const bool small = valid && deg > 0 && deg < rc.tn.warp_thresh && deg < split;
   uint32_t total = 0;
   const uint32_t excl = cta_excl_scan<CTA>(sm, small ? deg : 0u, total);
   if (total > 0) {
@@ -497,29 +695,54 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
     sm.s_val[tid] = val;
     sm.s_q[tid] = q;
     __syncthreads();
-    for (uint32_t base = 0; base < total; base += CTA) {
-      const uint32_t e = base + tid;
-      bool p = false;
-      uint32_t pv = 0;
-      if (e < total) {
-        uint32_t lo = 0, hi = CTA - 1;
-        while (lo < hi) {
-          const uint32_t md = (lo + hi + 1) >> 1;
-          if (sm.s_off[md] <= e) lo = md;
-          else hi = md - 1;
+    constexpr uint32_t E = 4;  // edges per thread per strip (strided by CTA: coalesced per k)
+    for (uint32_t base = 0; base < total; base += E * CTA) {
+      uint32_t own[E], v[E], cur[E], sb[E], op[E];
+      int32_t wt[E];
+#pragma unroll
+      for (uint32_t k = 0; k < E; ++k) {
+        const uint32_t e = base + k * CTA + tid;
+        own[k] = 0;
+        if (e < total) {
+          uint32_t lo = 0, hi = CTA - 1;
+          while (lo < hi) {
+            const uint32_t md = (lo + hi + 1) >> 1;
+            if (sm.s_off[md] <= e) lo = md;
+            else hi = md - 1;
+          }
+          own[k] = lo;
         }
-        const uint32_t oq = sm.s_q[lo];
-        const uint32_t edge = sm.s_beg[lo] + (e - sm.s_off[lo]);
-        const uint32_t op = g.op(oq);
-        const uint32_t sb = g.sbase(oq);
-        const uint32_t v = __ldg(g.colp(oq) + edge);
-        const int32_t wt = needs_w<OP>(op) ? __ldg(g.wp(oq) + edge) : 0;
-        p = relax<OP>(op, g.state + sb, g.stamp + sb, v, sm.s_val[lo], wt, rc.ep);
-        pv = sb + v;
-        if (RED == RED_ALL && p) sm.pushed[lo] = 1;
       }
-      push1<CTA>(sm, rc.out, p, pv);
-      pushed |= p;
+#pragma unroll
+      for (uint32_t k = 0; k < E; ++k) {
+        const uint32_t e = base + k * CTA + tid;
+        v[k] = 0;
+        wt[k] = 0;
+        sb[k] = 0;
+        op[k] = OP_BFS;
+        if (e < total) {
+          const uint32_t oq = sm.s_q[own[k]];
+          const uint32_t edge = sm.s_beg[own[k]] + (e - sm.s_off[own[k]]);
+          op[k] = g.op(oq);
+          sb[k] = g.sbase(oq);
+          v[k] = __ldg(g.colp(oq) + edge);
+          if (needs_w<OP>(op[k])) wt[k] = __ldg(g.wp(oq) + edge);
+        }
+      }
+#pragma unroll
+      for (uint32_t k = 0; k < E; ++k) cur[k] = (base + k * CTA + tid < total) ? __ldcg(g.state + sb[k] + v[k]) : 0u;
+      uint32_t f = 0;
+#pragma unroll
+      for (uint32_t k = 0; k < E; ++k) {
+        if (base + k * CTA + tid < total &&
+            decide<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], sm.s_val[own[k]], wt[k], cur[k], rc.ep)) {
+          f |= 1u << k;
+          if (RED == RED_ALL) sm.pushed[own[k]] = 1;
+          if (V::kBatched) g.mark(sm.s_q[own[k]], rc.ep);
+        }
+      }
+      push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
+      pushed |= f != 0;
       if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
     }
   }
@@ -533,22 +756,27 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
   if (full) flush_stage<CTA>(sm, rc.out);
 }
 
-// ForAll over the in-worklist: CTAs grab `chunk` tiles of CTA items at a time.
+// ForAll over the in-worklist (Sec. 3.1): the first `chunk` tiles of CTA items
+// of each CTA are static (blockIdx-th span); the rest is grabbed dynamically
+// with one atomic per span, so small frontiers cost no contended atomic.
 template <uint32_t OP, int CTA, int RED, class V>
 __device__ __forceinline__ void round_body(const V& g, Smem<CTA>& sm, const RoundCtx& rc, uint32_t& edges,
                                            uint32_t& any_true, uint32_t& any_false) {
   const uint32_t span = CTA * rc.tn.chunk;
+  const uint32_t static_end = gridDim.x * span;
+  uint32_t gb = blockIdx.x * span;
   for (;;) {
-    if (threadIdx.x == 0) sm.grab_base = atomicAdd(rc.grab, span);
-    __syncthreads();
-    const uint32_t gb = sm.grab_base;
-    __syncthreads();
     if (gb >= rc.in_n) break;
     for (uint32_t t = 0; t < rc.tn.chunk; ++t) {
       const uint32_t tb = gb + t * CTA;
       if (tb >= rc.in_n) break;
       process_tile<OP, CTA, RED>(g, sm, rc, tb + threadIdx.x, edges, any_true, any_false);
     }
+    if (static_end >= rc.in_n) break;  // everything was covered by the static spans
+    __syncthreads();
+    if (threadIdx.x == 0) sm.grab_base = static_end + atomicAdd(rc.grab, span);
+    __syncthreads();
+    gb = sm.grab_base;
   }
   __syncthreads();
   flush_stage<CTA>(sm, rc.out);
@@ -556,37 +784,199 @@ __device__ __forceinline__ void round_body(const V& g, Smem<CTA>& sm, const Roun
 
 // ----------------------------------------------------------------------------- grid barrier
 
-// SyncRunningThreads: valid only because the launch is cooperative (all CTAs
-// co-resident). Arrival counter is monotonic within a launch; the spin is
-// bounded by timeout_ns and gives up as soon as any CTA reported an error.
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" : : "l"(p), "l"(v) : "memory");
+}
+
+// SyncRunningThreads (Sec. 3.4): valid only because the launch is cooperative,
+// so every CTA is resident. Each CTA arrives with one 64-bit atomic that also
+// carries the out-worklist slots it reserved this round and whether it
+// appended to the big list, so the last CTA to arrive knows the round's
+// outcome without further loads; it resets the arrival word and publishes
+// (generation, flags, out-worklist size) in a release word on another cache
+// line, which the waiting CTAs poll. The device error code is read alongside
+// the arrival (it is sticky, so a code set just before the last arrival is
+// published by the next barrier and always reaches the host). The wait is
+// bounded by timeout_ns and gives up early when another CTA timed out. With
+// one CTA the barrier is just __syncthreads. The caller clears
+// sm.round_pushes and sm.big_appended at the start of each round.
 template <int CTA>
-__device__ __forceinline__ bool grid_barrier(Smem<CTA>& sm, DevStatus* st, uint32_t& target,
-                                             unsigned long long timeout_ns) {
+__device__ __forceinline__ bool grid_barrier(Smem<CTA>& sm, DevStatus* st, uint32_t& gen, unsigned long long timeout_ns,
+                                             bool with_big = false) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    target += gridDim.x;
-    __threadfence();
-    atomicAdd(&st->bar_count, 1u);
-    uint32_t ok = 1;
-    const unsigned long long t0 = globaltimer_ns();
-    uint32_t spins = 0;
-    for (;;) {
-      const uint32_t c = ld_acquire_gpu(&st->bar_count);
-      if (static_cast<int32_t>(c - target) >= 0) break;
-      if ((++spins & 31u) == 0) {
-        if (__ldcg(&st->err) == DERR_BARRIER_TIMEOUT) { ok = 0; break; }
-        if (globaltimer_ns() - t0 > timeout_ns) {
-          set_err(&st->err, DERR_BARRIER_TIMEOUT);
-          ok = 0;
-          break;
+    ++gen;
+    uint32_t ok = 1, out = 0, flags = 0;
+    unsigned long long big = 0;
+    const unsigned long long mine = (static_cast<unsigned long long>(sm.round_pushes) << 32) |
+                                    (sm.big_appended ? (1ull << 16) : 0ull) | 1ull;
+    if (gridDim.x == 1) {
+      out = sm.round_pushes;
+      flags = __ldcg(&st->err) & 0x7Fu;
+      if (with_big && sm.big_appended) {
+        big = __ldcg(&st->big_ctr);
+        flags |= kRelBigFlag;
+        st->big_ctr = 0;
+      }
+    } else {
+      __threadfence();
+      const uint32_t err_seen = __ldcg(&st->err);
+      const unsigned long long old = atomicAdd(&st->arrive, mine);
+      const unsigned long long total = old + mine;
+      if ((total & 0xFFFFull) == gridDim.x) {
+        // last arrival: every CTA's pushes and big-list appends are in
+        out = static_cast<uint32_t>(total >> 32);
+        flags = err_seen & 0x7Fu;
+        if (with_big && ((total >> 16) & 0xFFFFull) != 0) {
+          __threadfence();
+          big = __ldcg(&st->big_ctr);
+          flags |= kRelBigFlag;
+          st->big_pub = big;
+          st->big_ctr = 0;  // the next appends come after the big phase
+        }
+        st->arrive = 0;
+        __threadfence();
+        st_release_gpu_u64(&st->rel, (static_cast<unsigned long long>(gen) << 40) |
+                                          (static_cast<unsigned long long>(flags) << 32) | out);
+      } else {
+        const unsigned long long t0 = globaltimer_ns();
+        uint32_t spins = 0;
+        for (;;) {
+          const unsigned long long r = ld_acquire_gpu_u64(&st->rel);
+          if (static_cast<uint32_t>(r >> 40) >= gen) {
+            out = static_cast<uint32_t>(r);
+            flags = static_cast<uint32_t>(r >> 32) & 0xFFu;
+            if (flags & kRelBigFlag) big = __ldcg(&st->big_pub);
+            break;
+          }
+          if ((++spins & 63u) == 0) {
+            if (__ldcg(&st->err) == DERR_BARRIER_TIMEOUT) { ok = 0; break; }
+            if (globaltimer_ns() - t0 > timeout_ns) {
+              set_err(&st->err, DERR_BARRIER_TIMEOUT);
+              ok = 0;
+              break;
+            }
+          }
         }
       }
+      __threadfence();
     }
-    __threadfence();
     sm.flag = ok;
+    sm.pub_out = out;
+    sm.pub_err = flags & 0x7Fu;
+    sm.pub_flags = flags & kRelBigFlag;
+    sm.pub_big = big;
   }
   __syncthreads();
   return sm.flag != 0;
+}
+
+// Largest i in [0, n) with off[i] <= x, for an increasing array with off[0] <= x:
+// the whole CTA samples CTA positions per step (one load each) and narrows the
+// interval by a factor CTA.
+template <int CTA>
+__device__ __forceinline__ uint32_t cta_search_le(const unsigned long long* off, uint32_t n, unsigned long long x) {
+  uint32_t a = 0, b = n;
+  while (b - a > 1) {
+    const uint32_t step = (b - a + CTA - 1) / CTA;
+    const uint32_t p = a + threadIdx.x * step;
+    const bool pred = p < b && __ldcg(off + p) <= x;
+    const uint32_t c = static_cast<uint32_t>(__syncthreads_count(pred));
+    const uint32_t na = a + (c - 1) * step;
+    b = min(b, na + step);
+    a = na;
+  }
+  return a;
+}
+
+// Big phase of a round: the concatenated edges of the big list are split into
+// gridDim.x equal ranges. Each CTA deals its range out to its threads, four
+// edges per thread per strip (strided by CTA so loads coalesce within a list),
+// and finds each edge's list by binary search over a shared-memory window of
+// list offsets; all loads of a strip are issued before its atomics.
+template <uint32_t OP, int CTA, class V>
+__device__ __forceinline__ void big_phase(const V& g, Smem<CTA>& sm, const RoundCtx& rc, unsigned long long pub) {
+  constexpr uint32_t W = Smem<CTA>::kBigWin;
+  constexpr uint32_t E = 4;
+  const uint32_t n = min(static_cast<uint32_t>(pub >> 40), rc.big.cap);
+  const unsigned long long tot = pub & kBigEdgeMask;
+  const unsigned long long lo = tot * blockIdx.x / gridDim.x, hi = tot * (blockIdx.x + 1) / gridDim.x;
+  const uint32_t tid = threadIdx.x;
+  if (n != 0 && lo < hi) {
+    uint32_t w0 = cta_search_le<CTA>(rc.big.off, n, lo);
+    unsigned long long pos = lo;
+    while (pos < hi && w0 < n) {
+      __syncthreads();  // previous window no longer read
+      // the window (W entries) may be larger than the CTA: strided load
+      for (uint32_t i = tid; i < W && w0 + i < n; i += CTA) {
+        sm.be[i] = __ldcg(rc.big.e + w0 + i);
+        sm.bo[i] = __ldcg(rc.big.off + w0 + i);
+      }
+      __syncthreads();
+      const uint32_t lim = min(W, n - w0);
+      const unsigned long long wend_all = sm.bo[lim - 1] + (sm.be[lim - 1].y - sm.be[lim - 1].x);
+      const unsigned long long wend = wend_all < hi ? wend_all : hi;
+      for (unsigned long long base = pos; base < wend; base += E * CTA) {
+        uint32_t own[E], v[E], cur[E], sb[E], op[E];
+        int32_t wt[E];
+#pragma unroll
+        for (uint32_t k = 0; k < E; ++k) {
+          const unsigned long long e = base + k * CTA + tid;
+          own[k] = 0;
+          if (e < wend) {
+            uint32_t a = 0, b = lim - 1;
+            while (a < b) {
+              const uint32_t md = (a + b + 1) >> 1;
+              if (sm.bo[md] <= e) a = md;
+              else b = md - 1;
+            }
+            own[k] = a;
+          }
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < E; ++k) {
+          const unsigned long long e = base + k * CTA + tid;
+          v[k] = 0;
+          wt[k] = 0;
+          sb[k] = 0;
+          op[k] = OP_BFS;
+          if (e < wend) {
+            const uint4 en = sm.be[own[k]];
+            const uint32_t edge = en.x + static_cast<uint32_t>(e - sm.bo[own[k]]);
+            op[k] = g.op(en.w);
+            sb[k] = g.sbase(en.w);
+            v[k] = __ldg(g.colp(en.w) + edge);
+            if (needs_w<OP>(op[k])) wt[k] = __ldg(g.wp(en.w) + edge);
+          }
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < E; ++k) cur[k] = (base + k * CTA + tid < wend) ? __ldcg(g.state + sb[k] + v[k]) : 0u;
+        uint32_t f = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < E; ++k) {
+          if (base + k * CTA + tid < wend) {
+            const uint4 en = sm.be[own[k]];
+            if (decide<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], en.z, wt[k], cur[k], rc.ep)) {
+              f |= 1u << k;
+              if (V::kBatched) g.mark(en.w, rc.ep);
+            }
+          }
+        }
+        push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
+        if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
+      }
+      pos = wend;
+      w0 += lim;
+    }
+  }
+  __syncthreads();
+  flush_stage<CTA>(sm, rc.out);
 }
 
 template <int CTA>
@@ -608,6 +998,8 @@ __device__ __forceinline__ void init_smem(Smem<CTA>& sm) {
   if (threadIdx.x == 0) {
     sm.stage_n = 0;
     sm.flag = 0;
+    sm.round_pushes = 0;
+    sm.big_appended = 0;
   }
   __syncthreads();
 }
@@ -644,20 +1036,58 @@ __device__ __forceinline__ void fill_state(uint32_t* state, uint32_t n, const ui
 
 // ----------------------------------------------------------------------------- kernels
 
+// Clean exit of a persistent launch: the last CTA out restores the
+// between-launch invariants (counters at 0) and publishes the outcome.
+template <int CTA>
+__device__ __forceinline__ void persistent_exit(DevStatus* st, bool ok, uint32_t rounds, uint32_t last_out, uint32_t ep0,
+                                                unsigned long long esum, uint32_t* cont, uint32_t cont_buf) {
+  if (threadIdx.x != 0) return;
+  atomicAdd(&st->edges, esum);
+  if (!ok) return;
+  __threadfence();
+  const uint32_t prev = atomicAdd(&st->exit_count, 1u);
+  if (prev == gridDim.x - 1) {
+    __threadfence();
+    if (cont) {
+      cont[0] = cont_buf;
+      cont[1] = last_out;
+    }
+    st->rounds = rounds;
+    st->last_out = last_out;
+    st->epoch = ep0 + rounds;  // round ids ep0 .. ep0 + rounds - 1 were used
+    for (int i = 0; i < 4; ++i) {
+      st->tail[i] = 0;
+      st->grab[i] = 0;
+    }
+    st->arrive = 0;
+    st->rel = 0;
+    st->big_ctr = 0;
+    st->exit_count = 0;
+    __threadfence();
+  }
+}
+
+__device__ __forceinline__ void trace_round(unsigned long long* trace, uint32_t cap, uint32_t r, uint32_t in_n,
+                                            uint32_t out_n) {
+  if (trace && r < cap && blockIdx.x == 0 && threadIdx.x == 0) {
+    trace[2 * r] = globaltimer_ns();
+    trace[2 * r + 1] = (static_cast<unsigned long long>(in_n) << 32) | out_n;
+  }
+}
+
 // Iteration-outlined Iterate: every round in one cooperative launch.
 template <uint32_t OP, int CTA>
 __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& sm) {
   init_smem<CTA>(sm);
   DevStatus* st = p.st;
-  const uint32_t G = gridDim.x;
-  uint32_t target = 0;
+  uint32_t gen = 0;
   const uint32_t ep0 = __ldcg(&st->epoch);
   const uint32_t init_n = p.init_count ? min(__ldcg(p.init_count), p.init_cap) : p.n;
   if (p.skip_cta == static_cast<int>(blockIdx.x)) return;  // test hook: never arrives
 
   SingleView<OP> g{p.row_ptr, p.col, p.w, p.state, p.stamp, p.n};
   uint32_t edges = 0, dummy_t = 0, dummy_f = 0;
-  uint32_t rounds = 0;
+  uint32_t rounds = 0, last_out = 0;
   bool ok = true;
 
   if (p.init_state) {
@@ -667,69 +1097,62 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
 #pragma unroll
     for (uint32_t i = 0; i < 8; ++i) srcs[i] = (small && i < init_n) ? __ldcg(p.init_items + i) : kInf;
     if (small) ns = init_n;
-    fill_state<OP>(p.state, p.n, srcs, ns, blockIdx.x * CTA + threadIdx.x, G * CTA);
+    fill_state<OP>(p.state, p.n, srcs, ns, blockIdx.x * CTA + threadIdx.x, gridDim.x * CTA);
     if (OP != OP_CC && !small) {
-      ok = grid_barrier<CTA>(sm, st, target, p.timeout_ns);
+      ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
       if (ok) {
-        for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < init_n; i += G * CTA) {
+        for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < init_n; i += gridDim.x * CTA) {
           const uint32_t s = p.init_items ? __ldcg(p.init_items + i) : i;
           if (s < p.n) __stcg(p.state + s, 0u);
         }
       }
     }
   }
-  if (ok) ok = grid_barrier<CTA>(sm, st, target, p.timeout_ns);
+  if (ok) ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
+  trace_round(p.trace, p.trace_cap, 0, init_n, 0);
 
-  uint32_t last_out = 0;
+  uint32_t in_n = init_n;
   for (uint32_t r = 0; ok; ++r) {
-    RoundCtx rc;
-    rc.in_n = r == 0 ? init_n : min(__ldcg(&st->tail[r % 3]), p.cap);
     uint32_t* const cur = (r & 1) ? p.items[1] : p.items[0];  // no dynamic index into the param struct
     uint32_t* const nxt = (r & 1) ? p.items[0] : p.items[1];
+    RoundCtx rc;
+    rc.in_n = in_n;
     rc.in_items = r == 0 ? p.init_items : cur;
     rc.out = Out{nxt, &st->tail[(r + 1) % 3], p.cap, &st->err};
     rc.bfs_val = r + 1;
     rc.ep = ep0 + r;
     rc.grab = &st->grab[r % 3];
     rc.tn = p.tn;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      st->tail[(r + 2) % 3] = 0;
-      st->grab[(r + 2) % 3] = 0;
+    rc.big = p.big;
+    rc.big_ctr = &st->big_ctr;
+    if (threadIdx.x == 0) {
+      if (blockIdx.x == 0) {
+        st->tail[(r + 2) % 3] = 0;
+        st->grab[(r + 2) % 3] = 0;
+      }
+      sm.round_pushes = 0;
+      sm.big_appended = 0;
     }
     round_body<OP, CTA, RED_NONE>(g, sm, rc, edges, dummy_t, dummy_f);
-    ok = grid_barrier<CTA>(sm, st, target, p.timeout_ns);
+    ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns, p.big.cap != 0);
     if (!ok) break;
-    last_out = __ldcg(&st->tail[(r + 1) % 3]);
-    const uint32_t err = __ldcg(&st->err);
+    if (sm.pub_flags & kRelBigFlag) {
+      big_phase<OP, CTA>(g, sm, rc, sm.pub_big);
+      ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
+      if (!ok) break;
+    }
+    last_out = sm.pub_out;
     rounds = r + 1;
-    if (last_out == 0 || err != DERR_NONE) break;
+    trace_round(p.trace, p.trace_cap, rounds, in_n, last_out);
+    if (last_out == 0 || sm.pub_err != DERR_NONE) break;
     if (rounds >= p.max_rounds) {
       if (blockIdx.x == 0 && threadIdx.x == 0) set_err(&st->err, DERR_MAX_ROUNDS);
       break;
     }
+    in_n = min(last_out, p.cap);
   }
-
   const unsigned long long esum = cta_sum_u64<CTA>(sm, edges);
-  if (threadIdx.x == 0) {
-    atomicAdd(&st->edges, esum);
-    if (ok) {
-      __threadfence();
-      const uint32_t prev = atomicAdd(&st->exit_count, 1u);
-      if (prev == G - 1) {
-        __threadfence();
-        st->rounds = rounds;
-        st->last_out = last_out;
-        st->epoch = ep0 + rounds + 1;
-        for (int i = 0; i < 4; ++i) {
-          st->tail[i] = 0;
-          st->grab[i] = 0;
-        }
-        st->bar_count = 0;
-        st->exit_count = 0;
-        __threadfence();
-      }
-    }
-  }
+  persistent_exit<CTA>(st, ok, rounds, last_out, ep0, esum, nullptr, 0);
 }
 
 // One invocation (Invoke, or one round of a per-launch Iterate).
@@ -747,6 +1170,8 @@ __device__ __forceinline__ void invoke_round(const KParams& p, const RoundArgs& 
   rc.ep = ep;
   rc.grab = &st->grab[0];
   rc.tn = p.tn;
+  rc.big = BigList{nullptr, nullptr, 0};  // one launch, no grid barrier: long lists stay in the CTA bin
+  rc.big_ctr = nullptr;
   uint32_t edges = 0, any_true = 0, any_false = 0;
   round_body<OP, CTA, RED>(g, sm, rc, edges, any_true, any_false);
   const int t = __syncthreads_or(any_true != 0);
@@ -769,6 +1194,172 @@ __device__ __forceinline__ void invoke_round(const KParams& p, const RoundArgs& 
       if (OP != OP_BFS) st->epoch = ep + 1;
       st->exit_count = 0;
       __threadfence();
+    }
+  }
+}
+
+// Batched Iterate over many queries in one cooperative launch. Round 0 pops
+// the pending worklist left by the admission kernels (or by the previous
+// epoch); the launch stops when the worklist drains or after max_rounds
+// rounds (an epoch), leaving the pending items and their buffer in p.cont.
+template <int CTA>
+__device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& bs) {
+  Smem<CTA>& sm = bs.core;
+  init_smem<CTA>(sm);
+  const uint32_t nq = min(p.nq, static_cast<uint32_t>(kMaxBatchQueries));
+  for (uint32_t i = threadIdx.x; i < nq; i += CTA) bs.sbases[i] = __ldg(p.sbases + i);
+  __syncthreads();
+  DevStatus* st = p.st;
+  uint32_t gen = 0;
+  const uint32_t ep0 = __ldcg(&st->epoch);
+  const uint32_t cur0 = __ldcg(p.cont) & 1u;
+  const uint32_t init_n = nq == 0 ? 0u : min(__ldcg(p.cont + 1), p.cap);
+  BatchView g{p.desc, bs.sbases, nq, p.state, p.stamp, p.qlast};
+  uint32_t edges = 0, dummy_t = 0, dummy_f = 0, rounds = 0, last_out = 0;
+  bool ok = true;
+  trace_round(p.trace, p.trace_cap, 0, init_n, 0);
+  uint32_t in_n = init_n;
+  for (uint32_t r = 0; ok; ++r) {
+    RoundCtx rc;
+    rc.in_n = in_n;
+    const uint32_t b = (cur0 + r) & 1u;
+    rc.in_items = b ? p.items[1] : p.items[0];
+    rc.out = Out{b ? p.items[0] : p.items[1], &st->tail[(r + 1) % 3], p.cap, &st->err};
+    rc.bfs_val = 0;
+    rc.ep = ep0 + r;
+    rc.grab = &st->grab[r % 3];
+    rc.tn = p.tn;
+    rc.big = p.big;
+    rc.big_ctr = &st->big_ctr;
+    if (threadIdx.x == 0) {
+      if (blockIdx.x == 0) {
+        st->tail[(r + 2) % 3] = 0;
+        st->grab[(r + 2) % 3] = 0;
+      }
+      sm.round_pushes = 0;
+      sm.big_appended = 0;
+    }
+    round_body<OP_RUNTIME, CTA, RED_NONE>(g, sm, rc, edges, dummy_t, dummy_f);
+    ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns, p.big.cap != 0);
+    if (!ok) break;
+    if (sm.pub_flags & kRelBigFlag) {
+      big_phase<OP_RUNTIME, CTA>(g, sm, rc, sm.pub_big);
+      ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
+      if (!ok) break;
+    }
+    last_out = sm.pub_out;
+    rounds = r + 1;
+    trace_round(p.trace, p.trace_cap, rounds, in_n, last_out);
+    if (last_out == 0 || sm.pub_err != DERR_NONE) break;
+    if (rounds >= p.max_rounds) {
+      if (p.rounds_cap_is_error && blockIdx.x == 0 && threadIdx.x == 0) set_err(&st->err, DERR_MAX_ROUNDS);
+      break;
+    }
+    in_n = min(last_out, p.cap);
+  }
+  const unsigned long long esum = cta_sum_u64<CTA>(sm, edges);
+  persistent_exit<CTA>(st, ok, rounds, last_out, ep0, esum, p.cont, (cur0 + rounds) & 1u);
+}
+
+// Admission of new queries into a batch: per new query j, arena range
+// [base_j, base_j + n_j) gets its Iterate initial values (BFS/SSSP: INF; CC:
+// label v and every vertex on the pending worklist), then its sources get 0
+// and go onto the pending worklist.
+struct QNew {
+  uint32_t base;
+  uint32_t n;
+  uint32_t op;
+  uint32_t slot;
+  uint32_t src_off;  // first source in the flat source array
+  uint32_t nsrc;
+  uint32_t pre;      // exclusive prefix of n over the new queries
+  uint32_t pad;
+};
+
+struct AdmitParams {
+  const QNew* qn;
+  uint32_t nnew;
+  uint32_t total;         // sum of n over the new queries
+  const uint32_t* srcs;   // flat sources (vertex ids local to each query's graph)
+  uint32_t* state;
+  uint32_t* qlast;
+  uint32_t* items[2];
+  uint32_t cap;
+  uint32_t* cont;
+  DevStatus* st;
+};
+
+__device__ __forceinline__ uint32_t find_new(const QNew* qn, uint32_t nnew, uint32_t i) {
+  uint32_t lo = 0, hi = nnew - 1;
+  while (lo < hi) {
+    const uint32_t md = (lo + hi + 1) >> 1;
+    if (__ldg(&qn[md].pre) <= i) lo = md;
+    else hi = md - 1;
+  }
+  return lo;
+}
+
+// Warp-aggregated append of one optional item per lane to the pending worklist.
+__device__ __forceinline__ void append_pending(const AdmitParams& a, uint32_t* buf, bool p, uint32_t v) {
+  const unsigned m = __ballot_sync(kFull, p);
+  if (m == 0) return;
+  const uint32_t lane = threadIdx.x & 31;
+  const int ld = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == static_cast<uint32_t>(ld)) base = atomicAdd(a.cont + 1, static_cast<uint32_t>(__popc(m)));
+  base = __shfl_sync(kFull, base, ld);
+  if (p) {
+    const uint32_t idx = base + __popc(m & lanemask_lt());
+    if (idx < a.cap) __stcg(buf + idx, v);
+    else set_err(&a.st->err, DERR_WL_OVERFLOW);
+  }
+}
+
+__device__ __forceinline__ void admit_fill(const AdmitParams& a) {
+  // grid-stride over the concatenated new ranges; trip count uniform per warp
+  const uint32_t nthreads = gridDim.x * blockDim.x;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t* buf = (__ldcg(a.cont) & 1u) ? a.items[1] : a.items[0];
+  for (uint32_t base = tid - (threadIdx.x & 31); base < a.total; base += nthreads) {
+    const uint32_t i = base + (threadIdx.x & 31);
+    bool push = false;
+    uint32_t item = 0;
+    if (i < a.total) {
+      const uint32_t j = find_new(a.qn, a.nnew, i);
+      const QNew q = a.qn[j];
+      const uint32_t v = i - q.pre;
+      item = q.base + v;
+      __stcg(a.state + item, q.op == OP_CC ? v : kInf);
+      push = q.op == OP_CC;
+    }
+    append_pending(a, buf, push, item);
+  }
+}
+
+__device__ __forceinline__ void admit_sources(const AdmitParams& a) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nthreads = gridDim.x * blockDim.x;
+  uint32_t* buf = (__ldcg(a.cont) & 1u) ? a.items[1] : a.items[0];
+  const uint32_t ep = __ldcg(&a.st->epoch);
+  for (uint32_t j = tid; j < a.nnew; j += nthreads) a.qlast[a.qn[j].slot] = ep - 1u;
+  // one warp per new query walks its sources
+  const uint32_t warp = tid >> 5, nwarps = nthreads >> 5, lane = threadIdx.x & 31;
+  for (uint32_t j = warp; j < a.nnew; j += nwarps) {
+    const QNew q = a.qn[j];
+    if (q.op == OP_CC) continue;
+    for (uint32_t k0 = 0; k0 < q.nsrc; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      bool p = false;
+      uint32_t item = 0;
+      if (k < q.nsrc) {
+        const uint32_t v = __ldg(a.srcs + q.src_off + k);
+        if (v < q.n) {
+          item = q.base + v;
+          // a repeated source is pushed once
+          p = atomicExch(a.state + item, 0u) != 0u;
+        }
+      }
+      append_pending(a, buf, p, item);
     }
   }
 }

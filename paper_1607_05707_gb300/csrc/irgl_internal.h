@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <unordered_map>
 
@@ -20,16 +21,22 @@ struct irgl_ctx {
   irgl::DevStatus* st_host = nullptr;  // pinned mirror
   uint32_t* ws_items[2] = {nullptr, nullptr};  // Iterate scratch worklists
   uint32_t ws_cap = 0;
+  uint4* big_e = nullptr;               // big list of long adjacency lists (persistent kernels)
+  unsigned long long* big_off = nullptr;
+  uint32_t big_cap = 0;
   uint32_t* ws_stamp = nullptr;  // SSSP/CC push dedup stamps
   uint32_t ws_stamp_n = 0;
   uint32_t* ws_state = nullptr;  // result buffer of irgl_run with a host output
   uint32_t ws_state_n = 0;
   irgl_worklist* run_wl = nullptr;  // sources of irgl_run
   std::unordered_map<int, int> occ;  // occupancy cache
+  unsigned long long* trace = nullptr;  // per-round trace (2 words per round)
+  uint32_t trace_cap = 0;
   // test hooks
   uint64_t dbg_timeout_us = 0;
   int dbg_skip_cta = -1;
   uint32_t dbg_cap = 0;
+  uint32_t dbg_big_cap = 0;
 };
 
 struct irgl_graph {
@@ -70,10 +77,13 @@ irgl_status resolve_tuning(const irgl_tuning* in, irgl_tuning* out);
 irgl_status read_status(irgl_ctx* ctx, DevStatus* out);
 void reset_status(irgl_ctx* ctx);
 irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp);
+uint32_t big_capacity(uint64_t n);
+cudaError_t alloc_big(uint32_t cap, uint4** e, unsigned long long** off);
 int occupancy(irgl_ctx* ctx, int kind, uint32_t op, uint32_t cta, int red);
 uint32_t persistent_grid(irgl_ctx* ctx, uint32_t op, const irgl_tuning& t);
 irgl_status check_kernel_graph(irgl_kernel k, const irgl_graph* g);
 KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tuning& t);
+irgl_status tune_descend(const std::function<float(const irgl_tuning&)>& measure, irgl_tuning* best, float* best_ms);
 
 }  // namespace irgl
 

@@ -23,6 +23,11 @@ cudaError_t launch_init_state(uint32_t op, const KParams& p, uint32_t grid, cuda
 cudaError_t launch_wl_append(uint32_t* items, uint32_t* tail, uint32_t cap, const uint32_t* src, uint32_t k,
                              uint32_t* err, cudaStream_t s);
 
+// Batched multi-query Iterate (cooperative) and query admission.
+cudaError_t launch_batch_iterate(uint32_t cta, uint32_t grid, const BParams& p, cudaStream_t s);
+cudaError_t occupancy_batch(uint32_t cta, int* blocks_per_sm);
+cudaError_t launch_admit(const AdmitParams& a, uint32_t grid, cudaStream_t s);
+
 inline bool valid_cta(uint32_t cta) { return cta == 128 || cta == 256 || cta == 512 || cta == 1024; }
 
 }  // namespace irgl

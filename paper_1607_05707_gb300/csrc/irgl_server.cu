@@ -1,0 +1,546 @@
+// Serving loop: continuous batching of BFS/SSSP queries into epochs of the
+// batched persistent kernel.
+//
+// A host worker thread repeats:
+//   1. admission: take queued queries in arrival order while a slot is free and
+//      the query's state (16 bytes per vertex: state, stamp, two worklist
+//      entries) fits in the device arena (first-fit over free ranges); the
+//      arena is sized from free HBM when the server starts;
+//   2. upload the sorted descriptor table of the active queries and the new
+//      queries' sources; the admission kernels write their initial values and
+//      append their sources to the pending worklist, which still holds the
+//      unfinished work of the queries already running;
+//   3. one epoch: the batched persistent kernel runs at most epoch_rounds
+//      rounds over the union of all active queries' worklist items;
+//   4. queries that pushed nothing in the epoch's last round are finished:
+//      their result is copied to the caller's host buffer (or a scratch
+//      buffer), their completion time is stamped, and their arena range and
+//      slot are released.
+// The host/device boundary is crossed once per epoch and every device wait is
+// bounded, so no kernel spins indefinitely while the server idles.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "irgl.h"
+#include "irgl_internal.h"
+#include "irgl_launch.h"
+
+using namespace irgl;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_s() {
+  return std::chrono::duration<double>(Clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  uint64_t ticket = 0;
+  irgl_graph* g = nullptr;
+  uint32_t op = 0;
+  uint32_t src = 0;
+  uint32_t* host_out = nullptr;
+  double t_submit = 0;
+};
+
+struct Active {
+  Request rq;
+  uint32_t slot = 0;
+  uint32_t base = 0;
+  uint32_t n = 0;
+  uint32_t epochs = 0;
+  uint32_t ep_admit = 0;  // device epoch when admitted (round id base)
+};
+
+struct Done {
+  int32_t status = IRGL_OK;
+  uint32_t rounds = 0;
+  double t_submit = 0;
+  double t_done = 0;
+  uint64_t edges = 0;  // out-edges of reached vertices (when counting is on)
+};
+
+// First-fit allocator over [0, cap) in entries.
+struct Arena {
+  std::map<uint64_t, uint64_t> free_;  // base -> size
+  uint64_t cap = 0;
+  void init(uint64_t c) {
+    cap = c;
+    free_.clear();
+    if (c) free_[0] = c;
+  }
+  bool alloc(uint64_t n, uint64_t* base) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *base = it->first;
+        const uint64_t rest = it->second - n;
+        const uint64_t nb = it->first + n;
+        free_.erase(it);
+        if (rest) free_[nb] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t base, uint64_t n) {
+    if (n == 0) return;
+    auto it = free_.emplace(base, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+}  // namespace
+
+// Out-edges of reached vertices of one finished query: sum of out-degrees over
+// state[v] != INF (measurement only).
+__global__ void k_reached_edges(const uint32_t* __restrict__ state, const uint32_t* __restrict__ row_ptr, uint32_t n,
+                                unsigned long long* out) {
+  unsigned long long s = 0;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (__ldcg(state + v) != kInf) s += __ldg(row_ptr + v + 1) - __ldg(row_ptr + v);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+struct irgl_server {
+  irgl_ctx* ctx = nullptr;
+  irgl_server_config cfg{};
+  cudaStream_t stream = nullptr;
+  // device
+  DevStatus* st = nullptr;
+  DevStatus* st_host = nullptr;
+  uint32_t* state = nullptr;
+  uint32_t* stamp = nullptr;
+  uint32_t* items[2] = {nullptr, nullptr};
+  uint32_t* qlast = nullptr;
+  uint32_t* cont = nullptr;
+  QDesc* desc = nullptr;
+  uint32_t* sbases = nullptr;
+  QNew* qnew = nullptr;
+  uint32_t* srcs = nullptr;
+  unsigned long long* edge_cnt = nullptr;
+  uint4* big_e = nullptr;
+  unsigned long long* big_off = nullptr;
+  uint32_t big_cap = 0;
+  // pinned staging
+  QDesc* h_desc = nullptr;
+  uint32_t* h_sbases = nullptr;
+  QNew* h_qnew = nullptr;
+  uint32_t* h_srcs = nullptr;
+  uint32_t* h_qlast = nullptr;
+  unsigned long long* h_edges = nullptr;
+  uint32_t* h_scratch = nullptr;  // result sink for queries without a host buffer
+  uint64_t scratch_n = 0;
+  uint64_t arena_n = 0;
+  uint32_t grid = 0;
+  irgl_tuning t{};
+  Arena arena;
+  std::vector<uint32_t> free_slots;
+  std::vector<Active> active;  // sorted by base
+  // queue and results
+  std::mutex mu;
+  std::condition_variable cv;
+  std::condition_variable cv_done;
+  std::deque<Request> queue;
+  std::unordered_map<uint64_t, Done> done;
+  uint64_t next_ticket = 1;
+  uint64_t submitted = 0, completed = 0, rejected = 0, epochs = 0, rounds_total = 0;
+  uint64_t edges_total = 0;
+  double busy_s = 0;
+  int32_t fatal = IRGL_OK;
+  bool stop = false;
+  std::thread worker;
+};
+
+namespace {
+
+void server_free(irgl_server* s) {
+  cudaFree(s->st);
+  cudaFree(s->state);
+  cudaFree(s->stamp);
+  cudaFree(s->items[0]);
+  cudaFree(s->items[1]);
+  cudaFree(s->qlast);
+  cudaFree(s->cont);
+  cudaFree(s->desc);
+  cudaFree(s->sbases);
+  cudaFree(s->qnew);
+  cudaFree(s->srcs);
+  cudaFree(s->edge_cnt);
+  cudaFree(s->big_e);
+  cudaFree(s->big_off);
+  if (s->st_host) cudaFreeHost(s->st_host);
+  if (s->h_desc) cudaFreeHost(s->h_desc);
+  if (s->h_sbases) cudaFreeHost(s->h_sbases);
+  if (s->h_qnew) cudaFreeHost(s->h_qnew);
+  if (s->h_srcs) cudaFreeHost(s->h_srcs);
+  if (s->h_qlast) cudaFreeHost(s->h_qlast);
+  if (s->h_edges) cudaFreeHost(s->h_edges);
+  if (s->h_scratch) cudaFreeHost(s->h_scratch);
+  if (s->stream) cudaStreamDestroy(s->stream);
+}
+
+// One scheduling step of the worker. Returns false when there was nothing to do.
+bool server_step(irgl_server* s) {
+  const uint32_t max_slots = s->cfg.max_slots;
+  std::vector<Active> fresh;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->queue.empty() && s->active.empty()) {
+      s->cv.wait_for(lk, std::chrono::milliseconds(2));
+      if (s->queue.empty()) return false;
+    }
+    while (!s->queue.empty() && !s->free_slots.empty()) {
+      Request& rq = s->queue.front();
+      uint64_t base = 0;
+      if (!s->arena.alloc(rq.g->n ? rq.g->n : 1, &base)) break;  // wait for memory to free up
+      Active a;
+      a.rq = rq;
+      a.slot = s->free_slots.back();
+      s->free_slots.pop_back();
+      a.base = static_cast<uint32_t>(base);
+      a.n = rq.g->n;
+      a.ep_admit = s->st_host->epoch;  // first round id of the next epoch
+      fresh.push_back(a);
+      s->queue.pop_front();
+    }
+  }
+  const double t0 = now_s();
+  cudaError_t e = cudaSuccess;
+  // admission of new queries: descriptors, sources, initial values, pending items
+  if (!fresh.empty()) {
+    uint32_t nsrc = 0, pre = 0;
+    for (size_t j = 0; j < fresh.size(); ++j) {
+      const Active& a = fresh[j];
+      s->h_qnew[j] = QNew{a.base, a.n, a.rq.op, a.slot, nsrc, 1, pre, 0};
+      s->h_srcs[nsrc++] = a.rq.src;
+      pre += a.n;
+    }
+    AdmitParams ap{};
+    ap.qn = s->qnew;
+    ap.nnew = static_cast<uint32_t>(fresh.size());
+    ap.total = pre;
+    ap.srcs = s->srcs;
+    ap.state = s->state;
+    ap.qlast = s->qlast;
+    ap.items[0] = s->items[0];
+    ap.items[1] = s->items[1];
+    ap.cap = static_cast<uint32_t>(s->arena_n);
+    ap.cont = s->cont;
+    ap.st = s->st;
+    e = cudaMemcpyAsync(s->qnew, s->h_qnew, sizeof(QNew) * fresh.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->srcs, s->h_srcs, sizeof(uint32_t) * nsrc, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = launch_admit(ap, static_cast<uint32_t>(s->ctx->sm_count) * 4, s->stream);
+    for (auto& a : fresh) s->active.push_back(a);
+    std::sort(s->active.begin(), s->active.end(), [](const Active& x, const Active& y) { return x.base < y.base; });
+  }
+  // descriptor table of every active query, sorted by base
+  const uint32_t nq = static_cast<uint32_t>(s->active.size());
+  for (uint32_t i = 0; i < nq; ++i) {
+    const Active& a = s->active[i];
+    s->h_desc[i] = QDesc{a.rq.g->row_ptr, a.rq.g->col, a.rq.g->w, a.n, a.rq.op, a.base, a.slot};
+    s->h_sbases[i] = a.base;
+  }
+  if (e == cudaSuccess && nq)
+    e = cudaMemcpyAsync(s->desc, s->h_desc, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && nq)
+    e = cudaMemcpyAsync(s->sbases, s->h_sbases, sizeof(uint32_t) * nq, cudaMemcpyHostToDevice, s->stream);
+  // one epoch
+  BParams bp{};
+  bp.desc = s->desc;
+  bp.sbases = s->sbases;
+  bp.nq = nq;
+  bp.state = s->state;
+  bp.stamp = s->stamp;
+  bp.qlast = s->qlast;
+  bp.items[0] = s->items[0];
+  bp.items[1] = s->items[1];
+  bp.cap = static_cast<uint32_t>(s->arena_n);
+  bp.cont = s->cont;
+  bp.st = s->st;
+  bp.tn = Tune{s->t.warp_thresh, s->t.cta_thresh, s->t.chunk};
+  bp.max_rounds = s->cfg.epoch_rounds;
+  bp.rounds_cap_is_error = 0;
+  bp.timeout_ns = 2000000000ull;
+  bp.big = (s->t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{s->big_e, s->big_off, s->big_cap};
+  if (e == cudaSuccess && nq) e = launch_batch_iterate(s->t.cta_size, s->grid, bp, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->st_host, s->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess && nq) e = cudaMemcpyAsync(s->h_qlast, s->qlast, sizeof(uint32_t) * max_slots,
+                                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess || s->st_host->err != DERR_NONE) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->fatal = e != cudaSuccess ? IRGL_ERR_CUDA
+                                : (s->st_host->err == DERR_WL_OVERFLOW ? IRGL_ERR_WL_OVERFLOW : IRGL_ERR_BARRIER_TIMEOUT);
+    s->stop = true;
+    s->cv_done.notify_all();
+    return false;
+  }
+  const uint32_t rounds = s->st_host->rounds;
+  const uint32_t last_ep = s->st_host->epoch - 1;  // round id of the epoch's last round
+  // finished queries: no push in the last round
+  std::vector<Active> keep, fin;
+  for (auto& a : s->active) {
+    ++a.epochs;
+    if (nq == 0 || s->h_qlast[a.slot] < last_ep || rounds == 0) fin.push_back(a);
+    else keep.push_back(a);
+  }
+  // result sink for queries without a caller buffer (only this thread touches it)
+  uint64_t need = 0;
+  for (auto& a : fin)
+    if (!a.rq.host_out) need = std::max<uint64_t>(need, a.n);
+  if (need > s->scratch_n && e == cudaSuccess) {
+    if (s->h_scratch) cudaFreeHost(s->h_scratch);
+    s->h_scratch = nullptr;
+    s->scratch_n = 0;
+    e = cudaMallocHost(&s->h_scratch, sizeof(uint32_t) * need);
+    if (e == cudaSuccess) s->scratch_n = need;
+  }
+  for (auto& a : fin) {
+    uint32_t* dst = a.rq.host_out ? a.rq.host_out : s->h_scratch;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst, s->state + a.base, sizeof(uint32_t) * (size_t)a.n, cudaMemcpyDeviceToHost, s->stream);
+    if (s->cfg.count_edges && e == cudaSuccess) {
+      e = cudaMemsetAsync(s->edge_cnt + a.slot, 0, sizeof(unsigned long long), s->stream);
+      if (e == cudaSuccess) {
+        k_reached_edges<<<static_cast<uint32_t>(s->ctx->sm_count), 256, 0, s->stream>>>(
+            s->state + a.base, a.rq.g->row_ptr, a.n, s->edge_cnt + a.slot);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->h_edges + a.slot, s->edge_cnt + a.slot, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s->stream);
+    }
+  }
+  if (!fin.empty() && e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  const double t_done = now_s();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->epochs += 1;
+    s->rounds_total += rounds;
+    s->busy_s += t_done - t0;
+    for (auto& a : fin) {
+      Done d;
+      d.status = e == cudaSuccess ? IRGL_OK : IRGL_ERR_CUDA;
+      d.rounds = s->h_qlast[a.slot] - a.ep_admit + 2;
+      d.t_submit = a.rq.t_submit;
+      d.t_done = t_done;
+      d.edges = s->cfg.count_edges ? s->h_edges[a.slot] : 0;
+      s->edges_total += d.edges;
+      s->done[a.rq.ticket] = d;
+      s->completed += 1;
+      s->arena.release(a.base, a.n ? a.n : 1);
+      s->free_slots.push_back(a.slot);
+    }
+    s->active.swap(keep);
+  }
+  if (!fin.empty()) s->cv_done.notify_all();
+  return true;
+}
+
+void server_loop(irgl_server* s) {
+  DeviceGuard guard(s->ctx->device);
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->stop) break;
+    }
+    server_step(s);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irgl_server** out) {
+  if (!ctx || !cfg || !out) return fail(IRGL_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (cfg->max_slots == 0 || cfg->max_slots > static_cast<uint32_t>(kMaxBatchQueries))
+    return fail(IRGL_ERR_INVALID_ARG, "max_slots must be in 1..%d", kMaxBatchQueries);
+  if (cfg->epoch_rounds == 0) return fail(IRGL_ERR_INVALID_ARG, "epoch_rounds must be > 0");
+  DeviceGuard guard(ctx->device);
+  irgl_tuning t;
+  irgl_status st = resolve_tuning(&cfg->tuning, &t);
+  if (st != IRGL_OK) return st;
+  irgl_server* s = new (std::nothrow) irgl_server();
+  if (!s) return fail(IRGL_ERR_OOM, "server allocation");
+  s->ctx = ctx;
+  s->cfg = *cfg;
+  s->t = t;
+  uint64_t bytes = cfg->arena_bytes;
+  if (bytes == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    bytes = static_cast<uint64_t>(fr * 0.4);
+  }
+  s->arena_n = std::min<uint64_t>(bytes / 16, 0xFFFFFFF0ull);
+  const uint32_t S = cfg->max_slots;
+  cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&s->st, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaMallocHost(&s->st_host, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaMalloc(&s->state, sizeof(uint32_t) * s->arena_n);
+  if (e == cudaSuccess) e = cudaMalloc(&s->stamp, sizeof(uint32_t) * s->arena_n);
+  if (e == cudaSuccess) e = cudaMalloc(&s->items[0], sizeof(uint32_t) * s->arena_n);
+  if (e == cudaSuccess) e = cudaMalloc(&s->items[1], sizeof(uint32_t) * s->arena_n);
+  if (e == cudaSuccess) e = cudaMalloc(&s->qlast, sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMalloc(&s->cont, 128);
+  if (e == cudaSuccess) e = cudaMalloc(&s->desc, sizeof(QDesc) * S);
+  if (e == cudaSuccess) e = cudaMalloc(&s->sbases, sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMalloc(&s->qnew, sizeof(QNew) * S);
+  if (e == cudaSuccess) e = cudaMalloc(&s->srcs, sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMalloc(&s->edge_cnt, sizeof(unsigned long long) * S);
+  if (e == cudaSuccess) {
+    s->big_cap = big_capacity(s->arena_n);
+    e = alloc_big(s->big_cap, &s->big_e, &s->big_off);
+  }
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_desc, sizeof(QDesc) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_sbases, sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_qnew, sizeof(QNew) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_srcs, sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_qlast, sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_edges, sizeof(unsigned long long) * S);
+  if (e != cudaSuccess) {
+    server_free(s);
+    delete s;
+    return cuda_fail(e, "server allocation");
+  }
+  DevStatus z;
+  std::memset(&z, 0, sizeof(z));
+  z.epoch = 1;
+  *s->st_host = z;
+  e = cudaMemcpyAsync(s->st, s->st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->stamp, 0, sizeof(uint32_t) * s->arena_n, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->cont, 0, 128, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->qlast, 0, sizeof(uint32_t) * S, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  int nb = 0;
+  if (e == cudaSuccess) e = occupancy_batch(t.cta_size, &nb);
+  if (e != cudaSuccess || nb <= 0) {
+    server_free(s);
+    delete s;
+    return e != cudaSuccess ? cuda_fail(e, "server setup") : fail(IRGL_ERR_CUDA, "batched kernel cannot be resident");
+  }
+  if (t.blocks_per_sm && static_cast<int>(t.blocks_per_sm) < nb) nb = static_cast<int>(t.blocks_per_sm);
+  s->grid = static_cast<uint32_t>(nb) * static_cast<uint32_t>(ctx->sm_count);
+  if (t.max_blocks && t.max_blocks < s->grid) s->grid = t.max_blocks;
+  s->arena.init(s->arena_n);
+  for (uint32_t i = 0; i < S; ++i) s->free_slots.push_back(S - 1 - i);
+  s->worker = std::thread(server_loop, s);
+  *out = s;
+  return IRGL_OK;
+}
+
+irgl_status irgl_server_submit(irgl_server* s, irgl_graph* g, irgl_kernel k, uint32_t src, uint32_t* host_out,
+                               uint64_t* ticket) {
+  if (!s || !g || !ticket) return fail(IRGL_ERR_INVALID_ARG, "NULL argument");
+  if (k != IRGL_BFS && k != IRGL_SSSP) return fail(IRGL_ERR_UNSUPPORTED, "the server runs BFS and SSSP queries");
+  irgl_status st = check_kernel_graph(k, g);
+  if (st != IRGL_OK) return st;
+  if (src >= g->n) return fail(IRGL_ERR_INVALID_ARG, "source %u out of range", src);
+  if (g->ctx != s->ctx) return fail(IRGL_ERR_INVALID_ARG, "graph belongs to another context");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->fatal != IRGL_OK) return fail(s->fatal, "server stopped after a device error");
+  if (static_cast<uint64_t>(g->n) > s->arena_n) {
+    s->rejected += 1;
+    return fail(IRGL_ERR_ADMISSION, "query needs %u arena entries, the arena holds %llu", g->n,
+                (unsigned long long)s->arena_n);
+  }
+  Request rq;
+  rq.ticket = s->next_ticket++;
+  rq.g = g;
+  rq.op = static_cast<uint32_t>(k);
+  rq.src = src;
+  rq.host_out = host_out;
+  rq.t_submit = now_s();
+  s->queue.push_back(rq);
+  s->submitted += 1;
+  *ticket = rq.ticket;
+  s->cv.notify_one();
+  return IRGL_OK;
+}
+
+irgl_status irgl_server_poll(irgl_server* s, uint64_t ticket, irgl_query_info* info) {
+  if (!s) return fail(IRGL_ERR_INVALID_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->done.find(ticket);
+  if (it == s->done.end()) return s->fatal != IRGL_OK ? fail(s->fatal, "server stopped") : IRGL_ERR_NOT_READY;
+  if (info) {
+    info->status = it->second.status;
+    info->rounds = it->second.rounds;
+    info->latency_s = it->second.t_done - it->second.t_submit;
+    info->t_submit_s = it->second.t_submit;
+    info->t_done_s = it->second.t_done;
+    info->edges = it->second.edges;
+  }
+  return IRGL_OK;
+}
+
+irgl_status irgl_server_drain(irgl_server* s, uint32_t timeout_ms) {
+  if (!s) return fail(IRGL_ERR_INVALID_ARG, "server is NULL");
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms);
+  while (s->completed + s->rejected < s->submitted && s->fatal == IRGL_OK) {
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) return fail(IRGL_ERR_NOT_READY, "drain timed out");
+  }
+  if (s->fatal != IRGL_OK) return fail(s->fatal, "server stopped after a device error");
+  return IRGL_OK;
+}
+
+irgl_status irgl_server_stats(irgl_server* s, irgl_server_counters* out) {
+  if (!s || !out) return fail(IRGL_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  out->submitted = s->submitted;
+  out->completed = s->completed;
+  out->rejected = s->rejected;
+  out->epochs = s->epochs;
+  out->rounds = s->rounds_total;
+  out->edges = s->edges_total;
+  out->busy_s = s->busy_s;
+  out->active = static_cast<uint32_t>(s->active.size());
+  out->queued = static_cast<uint32_t>(s->queue.size());
+  out->arena_entries = s->arena_n;
+  out->grid = s->grid;
+  out->cta_size = s->t.cta_size;
+  return IRGL_OK;
+}
+
+irgl_status irgl_server_destroy(irgl_server* s) {
+  if (!s) return IRGL_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  DeviceGuard guard(s->ctx->device);
+  cudaStreamSynchronize(s->stream);
+  server_free(s);
+  delete s;
+  return IRGL_OK;
+}
+
+}  // extern "C"

@@ -37,6 +37,7 @@ IRGL_HOST_PTRS = 0x0
 IRGL_DEVICE_PTRS = 0x1
 IRGL_SYMMETRIC = 0x2
 IRGL_VALIDATE = 0x4
+IRGL_TUNE_NO_SPLIT = 0x1
 
 KERNELS = {"bfs": IRGL_BFS, "sssp": IRGL_SSSP, "cc": IRGL_CC}
 MODES = {"per_launch": IRGL_PER_LAUNCH, "persistent": IRGL_PERSISTENT}
@@ -50,6 +51,7 @@ class irgl_tuning(ctypes.Structure):
         ("chunk", c_uint32),
         ("blocks_per_sm", c_uint32),
         ("max_blocks", c_uint32),
+        ("flags", c_uint32),
     ]
 
     def as_dict(self) -> dict:
@@ -64,11 +66,46 @@ class irgl_stats(ctypes.Structure):
         ("launches", c_uint32),
         ("edges_scanned", c_uint64),
         ("last_out", c_uint32),
-        ("reserved", c_uint32),
+        ("device_ms", ctypes.c_float),
     ]
 
     def as_dict(self) -> dict:
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "device_ms"}
+        d["device_ms"] = float(self.device_ms)
+        return d
+
+
+class irgl_server_config(ctypes.Structure):
+    _fields_ = [
+        ("arena_bytes", c_uint64),
+        ("max_slots", c_uint32),
+        ("epoch_rounds", c_uint32),
+        ("count_edges", c_uint32),
+        ("reserved", c_uint32),
+        ("tuning", irgl_tuning),
+    ]
+
+
+class irgl_query_info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("rounds", c_uint32),
+        ("latency_s", ctypes.c_double),
+        ("t_submit_s", ctypes.c_double),
+        ("t_done_s", ctypes.c_double),
+        ("edges", c_uint64),
+    ]
+
+
+class irgl_server_counters(ctypes.Structure):
+    _fields_ = [
+        ("submitted", c_uint64), ("completed", c_uint64), ("rejected", c_uint64), ("epochs", c_uint64),
+        ("rounds", c_uint64), ("edges", c_uint64), ("busy_s", ctypes.c_double), ("active", c_uint32),
+        ("queued", c_uint32), ("arena_entries", c_uint64), ("grid", c_uint32), ("cta_size", c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: (float(getattr(self, k)) if k == "busy_s" else int(getattr(self, k))) for k, _ in self._fields_}
 
 
 class IrglError(RuntimeError):
@@ -105,6 +142,27 @@ _SIGS = {
     "irgl_ctx_sync": [_P, POINTER(irgl_stats)],
     "irgl_run": [_P, c_int, _P, _P, c_uint32, _P, c_int, c_int, POINTER(irgl_tuning), c_uint32, POINTER(irgl_stats)],
     "irgl_debug_set": [_P, c_int, c_int64],
+    "irgl_trace_enable": [_P, c_uint32],
+    "irgl_trace_read": [_P, _P, _P, _P, c_uint32, POINTER(c_uint32)],
+    "irgl_server_create": [_P, POINTER(irgl_server_config), POINTER(_P)],
+    "irgl_server_submit": [_P, _P, c_int, c_uint32, _P, POINTER(c_uint64)],
+    "irgl_server_poll": [_P, c_uint64, POINTER(irgl_query_info)],
+    "irgl_server_drain": [_P, c_uint32],
+    "irgl_server_stats": [_P, POINTER(irgl_server_counters)],
+    "irgl_server_destroy": [_P],
+    "irgl_autotune": [_P, c_int, _P, _P, c_uint32, c_uint32, POINTER(irgl_tuning), POINTER(ctypes.c_float)],
+    "irgl_batch_autotune": [_P, c_uint32, POINTER(irgl_tuning), POINTER(ctypes.c_float)],
+    "irgl_control_cta": [POINTER(c_uint32), c_uint32, c_uint32, POINTER(c_uint32)],
+    "irgl_batch_create": [_P, c_uint32, POINTER(_P)],
+    "irgl_batch_destroy": [_P],
+    "irgl_batch_add": [_P, _P, c_int, _P, c_uint32, POINTER(c_uint32)],
+    "irgl_batch_prepare": [_P, POINTER(irgl_tuning), c_int],
+    "irgl_batch_launch": [_P],
+    "irgl_batch_sync": [_P, POINTER(irgl_stats)],
+    "irgl_batch_run": [_P, POINTER(irgl_stats)],
+    "irgl_batch_info": [_P, POINTER(c_uint32), POINTER(c_uint32), POINTER(c_uint32), POINTER(c_int), POINTER(c_uint64)],
+    "irgl_batch_result": [_P, c_uint32, POINTER(_P), POINTER(c_uint32), POINTER(c_uint32)],
+    "irgl_batch_copy_result": [_P, c_uint32, _P],
 }
 _RESTYPE = {"irgl_last_error": c_char_p, "irgl_status_string": c_char_p}
 
@@ -273,3 +331,141 @@ def irgl_run(ctx: int, kernel: int, g: int, srcs_host: int | None, nsrc: int, st
 
 def irgl_debug_set(ctx: int, key: int, value: int) -> None:
     _check(lib().irgl_debug_set(ctx, key, value))
+
+
+def irgl_control_cta(masks, preferred: int = 0) -> int:
+    arr = (c_uint32 * max(len(masks), 1))(*masks)
+    out = c_uint32()
+    _check(lib().irgl_control_cta(arr, len(masks), preferred, ctypes.byref(out)))
+    return int(out.value)
+
+
+def irgl_batch_create(ctx: int, max_queries: int) -> int:
+    h = _P()
+    _check(lib().irgl_batch_create(ctx, max_queries, ctypes.byref(h)))
+    return h.value
+
+
+def irgl_batch_destroy(b: int) -> None:
+    _check(lib().irgl_batch_destroy(b))
+
+
+def irgl_batch_add(b: int, g: int, kernel: int, srcs_host: int | None, nsrc: int) -> int:
+    q = c_uint32()
+    _check(lib().irgl_batch_add(b, g, kernel, srcs_host, nsrc, ctypes.byref(q)))
+    return int(q.value)
+
+
+def irgl_batch_prepare(b: int, tuning=None, use_cuda_graph: int = 1) -> None:
+    _check(lib().irgl_batch_prepare(b, _tuning(tuning), use_cuda_graph))
+
+
+def irgl_batch_launch(b: int) -> None:
+    _check(lib().irgl_batch_launch(b))
+
+
+def irgl_batch_sync(b: int) -> dict:
+    st = irgl_stats()
+    _check(lib().irgl_batch_sync(b, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def irgl_batch_run(b: int) -> dict:
+    st = irgl_stats()
+    _check(lib().irgl_batch_run(b, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def irgl_batch_info(b: int) -> dict:
+    nq, grid, cta, arena = c_uint32(), c_uint32(), c_uint32(), c_uint64()
+    cap = c_int()
+    _check(lib().irgl_batch_info(b, ctypes.byref(nq), ctypes.byref(grid), ctypes.byref(cta), ctypes.byref(cap),
+                                 ctypes.byref(arena)))
+    return dict(nqueries=int(nq.value), grid=int(grid.value), cta_size=int(cta.value),
+                graph_captured=bool(cap.value), arena_entries=int(arena.value))
+
+
+def irgl_batch_result(b: int, query_id: int) -> tuple[int, int, int]:
+    p, n, r = _P(), c_uint32(), c_uint32()
+    _check(lib().irgl_batch_result(b, query_id, ctypes.byref(p), ctypes.byref(n), ctypes.byref(r)))
+    return int(p.value or 0), int(n.value), int(r.value)
+
+
+def irgl_batch_copy_result(b: int, query_id: int, host_out: int) -> None:
+    _check(lib().irgl_batch_copy_result(b, query_id, host_out))
+
+
+def irgl_trace_enable(ctx: int, max_rounds: int) -> None:
+    _check(lib().irgl_trace_enable(ctx, max_rounds))
+
+
+def irgl_trace_read(ctx: int, cap: int = 1 << 16):
+    """Per-round trace of the last persistent launch: (t_ns, in_n, out_n) numpy arrays."""
+    import numpy as np
+
+    t = np.zeros(cap, dtype=np.uint64)
+    a = np.zeros(cap, dtype=np.uint32)
+    b = np.zeros(cap, dtype=np.uint32)
+    n = c_uint32()
+    _check(lib().irgl_trace_read(ctx, t.ctypes.data, a.ctypes.data, b.ctypes.data, cap, ctypes.byref(n)))
+    k = int(n.value)
+    return t[:k], a[:k], b[:k]
+
+
+def irgl_server_create(ctx: int, arena_bytes: int = 0, max_slots: int = 256, epoch_rounds: int = 64,
+                       count_edges: int = 1, tuning=None) -> int:
+    cfg = irgl_server_config()
+    cfg.arena_bytes = arena_bytes
+    cfg.max_slots = max_slots
+    cfg.epoch_rounds = epoch_rounds
+    cfg.count_edges = count_edges
+    if tuning is not None:
+        for k, v in dict(tuning).items():
+            setattr(cfg.tuning, k, int(v))
+    h = _P()
+    _check(lib().irgl_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def irgl_server_submit(srv: int, g: int, kernel: int, src: int, host_out: int | None = None) -> int:
+    t = c_uint64()
+    _check(lib().irgl_server_submit(srv, g, kernel, src, host_out, ctypes.byref(t)))
+    return int(t.value)
+
+
+def irgl_server_poll(srv: int, ticket: int) -> dict | None:
+    info = irgl_query_info()
+    rc = lib().irgl_server_poll(srv, ticket, ctypes.byref(info))
+    if rc == IRGL_ERR_NOT_READY:
+        return None
+    _check(rc)
+    return dict(status=int(info.status), rounds=int(info.rounds), latency_s=float(info.latency_s),
+                t_submit_s=float(info.t_submit_s), t_done_s=float(info.t_done_s), edges=int(info.edges))
+
+
+def irgl_server_drain(srv: int, timeout_ms: int = 600000) -> None:
+    _check(lib().irgl_server_drain(srv, timeout_ms))
+
+
+def irgl_server_stats(srv: int) -> dict:
+    c = irgl_server_counters()
+    _check(lib().irgl_server_stats(srv, ctypes.byref(c)))
+    return c.as_dict()
+
+
+def irgl_server_destroy(srv: int) -> None:
+    _check(lib().irgl_server_destroy(srv))
+
+
+def irgl_autotune(ctx: int, kernel: int, g: int, srcs_host: int | None, nsrc: int, reps: int = 3) -> tuple[dict, float]:
+    t = irgl_tuning()
+    ms = ctypes.c_float()
+    _check(lib().irgl_autotune(ctx, kernel, g, srcs_host, nsrc, reps, ctypes.byref(t), ctypes.byref(ms)))
+    return t.as_dict(), float(ms.value)
+
+
+def irgl_batch_autotune(b: int, reps: int = 3) -> tuple[dict, float]:
+    t = irgl_tuning()
+    ms = ctypes.c_float()
+    _check(lib().irgl_batch_autotune(b, reps, ctypes.byref(t), ctypes.byref(ms)))
+    return t.as_dict(), float(ms.value)

@@ -1,0 +1,120 @@
+"""Batched multi-instance launches vs the oracle (bit-exact), with and without
+CUDA-graph replay, under several schedules; per-instance termination rounds."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_05707_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+INF = 0xFFFFFFFF
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_05707_gb300.api import Context
+
+    c = Context(0, torch.cuda.Stream())
+    yield c
+    c.close()
+
+
+def _instances():
+    rng = np.random.default_rng(17)
+    out = []
+    for i in range(24):
+        g = inputs.rmat(int(rng.integers(8, 14)), 8, seed=500 + i, weights=True)
+        srcs = inputs.sources(g, int(rng.integers(1, 5)), seed=600 + i)
+        out.append(("sssp" if i % 3 else "bfs", g, srcs))
+    m = inputs.mesh(60, 45, seed=3, del_frac=0.05, extra_frac=0.01, weights=True)
+    out.append(("cc", m, None))
+    out.append(("bfs", m, np.array([0], np.uint32)))
+    out.append(("sssp", m, np.array([17, 2000], np.uint32)))
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("tuning", [None, dict(cta_size=128, warp_thresh=4, cta_thresh=64, chunk=2),
+                                    dict(cta_size=512, warp_thresh=1 << 30, cta_thresh=1 << 30, max_blocks=5)])
+def test_batch_matches_oracle(ctx, use_graph, tuning):
+    from paper_1607_05707_gb300.api import Batch
+
+    inst = _instances()
+    graphs = [ctx.load(g) for _, g, _ in inst]
+    b = Batch(ctx, 64)
+    for (k, g, s), dg in zip(inst, graphs):
+        b.add(k, dg, s)
+    info = b.prepare(tuning, use_cuda_graph=use_graph)
+    if use_graph:
+        assert info["graph_captured"], "cooperative launch was not captured in a CUDA graph"
+    for rep in range(2):  # replays recompute everything from the sources
+        st = b.run()
+        assert st["rounds"] >= 1 and st["device_ms"] > 0
+        for q, (k, g, s) in enumerate(inst):
+            got, rounds = b.result(q)
+            want = oracle.run(k, g, s)
+            np.testing.assert_array_equal(got, want, err_msg=f"query {q} ({k}) rep {rep}")
+            if k == "bfs":
+                assert rounds == int(want[want != INF].max()) + 1
+    b.close()
+    for dg in graphs:
+        dg.close()
+
+
+def test_batch_alone_equals_mix(ctx):
+    from paper_1607_05707_gb300.api import Batch, as_u32
+
+    inst = _instances()[:8]
+    graphs = [ctx.load(g) for _, g, _ in inst]
+    b = Batch(ctx, 16)
+    for (k, g, s), dg in zip(inst, graphs):
+        b.add(k, dg, s)
+    b.prepare()
+    b.run()
+    for q, ((k, g, s), dg) in enumerate(zip(inst, graphs)):
+        alone, _ = ctx.run(k, dg, s)
+        got, _ = b.result(q)
+        np.testing.assert_array_equal(got, as_u32(alone)[: g.n])
+    b.close()
+
+
+def test_batch_config_sample(ctx):
+    # a sample of the 256-instance workload (R-MAT scale 10..18, edge factor 8, 1-4 sources, SSSP)
+    from paper_1607_05707_gb300.api import Batch
+
+    inst = inputs.workload_batch(count=20)
+    graphs = [ctx.load(g, validate=False) for g, _ in inst]
+    b = Batch(ctx, 32)
+    for (g, s), dg in zip(inst, graphs):
+        b.add("sssp", dg, s)
+    b.prepare()
+    b.run()
+    for q, (g, s) in enumerate(inst):
+        got, _ = b.result(q)
+        np.testing.assert_array_equal(got, oracle.sssp(g.n, g.row_ptr, g.col, g.w, s))
+    b.close()
+
+
+def test_trace_records_rounds(ctx):
+    from paper_1607_05707_gb300 import irgl as C
+    from paper_1607_05707_gb300.api import as_u32, trace
+
+    g, srcs = inputs.workload_grid64()
+    dg = ctx.load(g)
+    C.irgl_trace_enable(ctx.handle, 1024)
+    out, st = ctx.run("bfs", dg, srcs)
+    t, a, o = trace(ctx)
+    C.irgl_trace_enable(ctx.handle, 0)
+    assert len(t) == st["rounds"] + 1 == 128
+    assert (np.diff(t.astype(np.int64)) >= 0).all()
+    # round r pops the r-th anti-diagonal of the 64x64 grid (from the corner): min(r+1, 127-r) vertices
+    r = np.arange(0, 127)
+    np.testing.assert_array_equal(a[1:], np.minimum(r + 1, 127 - r))
+    assert o[-1] == 0
+    dg.close()

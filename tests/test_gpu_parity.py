@@ -25,6 +25,8 @@ SCHEDULES = [
     dict(cta_size=1024, warp_thresh=4, cta_thresh=64, chunk=3),
     dict(cta_size=256, warp_thresh=8, cta_thresh=128, chunk=2, max_blocks=3),
     dict(cta_size=128, warp_thresh=16, cta_thresh=512, max_blocks=1),
+    dict(cta_size=256, warp_thresh=32, cta_thresh=256, flags=1),  # long lists kept in the CTA bin (no split)
+    dict(cta_size=1024, warp_thresh=2, cta_thresh=8),             # most lists split over the grid
 ]
 
 
@@ -282,6 +284,20 @@ def test_errors_and_recovery(ctx):
     with pytest.raises(C.IrglError):
         ctx.run("bfs", dgu, [64])
     dgu.close()
+    dg.close()
+
+
+def test_big_list_overflow_falls_back(ctx):
+    # a big list of 3 entries: further long lists take the CTA-bin path in the same round
+    g = inputs.rmat(14, 16, seed=61, weights=True)
+    dg = ctx.load(g)
+    s = inputs.sources(g, 1, seed=62)
+    ctx.debug_set(4, 3)
+    try:
+        for k in ("bfs", "sssp"):
+            check(ctx, k, g, dg, s, "persistent", dict(cta_size=256, warp_thresh=4, cta_thresh=16))
+    finally:
+        ctx.debug_set(4, 0)
     dg.close()
 
 

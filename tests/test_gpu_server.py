@@ -1,0 +1,131 @@
+"""Serving loop: continuous batching with memory-based admission. Every query's
+result (alone, in a mix, admitted late, queued behind memory) is bit-exact
+against the oracle."""
+from __future__ import annotations
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_05707_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+INF = 0xFFFFFFFF
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_05707_gb300.api import Context
+
+    ctx = Context(0, torch.cuda.Stream())
+    graphs = [inputs.rmat(14, 16, seed=71, weights=True), inputs.rmat(12, 8, seed=72, weights=True)]
+    graphs += [inputs.mesh(s, s, seed=73 + s, del_frac=0.01, extra_frac=0.001, weights=True) for s in (64, 150, 301)]
+    dgs = [ctx.load(g, symmetric=False) for g in graphs]
+    yield ctx, graphs, dgs
+    for d in dgs:
+        d.close()
+    ctx.close()
+
+
+def _queries(graphs, k, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(k):
+        gi = int(rng.integers(0, len(graphs)))
+        g = graphs[gi]
+        src = int(inputs.sources(g, 1, seed=seed * 1000 + i)[0])
+        out.append(("bfs" if rng.random() < 0.7 else "sssp", gi, src))
+    return out
+
+
+def _check(graphs, q, buf, info):
+    kind, gi, src = q
+    g = graphs[gi]
+    want = oracle.run(kind, g, np.array([src], np.uint32))
+    np.testing.assert_array_equal(buf, want, err_msg=str(q))
+    assert info["status"] == 0 and info["latency_s"] > 0
+    if kind == "bfs":
+        assert info["rounds"] == int(want[want != INF].max()) + 1
+    deg = g.out_degree()
+    assert info["edges"] == int(deg[want != INF].sum())
+
+
+def test_server_mix_matches_oracle(env):
+    from paper_1607_05707_gb300.api import Server
+
+    ctx, graphs, dgs = env
+    qs = _queries(graphs, 60, seed=5)
+    srv = Server(ctx, arena_bytes=64 << 20, max_slots=32, epoch_rounds=16)
+    bufs, tickets = [], []
+    for kind, gi, src in qs:
+        b = np.empty(graphs[gi].n, dtype=np.uint32)
+        bufs.append(b)
+        tickets.append(srv.submit(kind, dgs[gi], src, b))
+    srv.drain(120)
+    st = srv.stats()
+    assert st["completed"] == len(qs) and st["rejected"] == 0 and st["epochs"] >= 1
+    for q, b, t in zip(qs, bufs, tickets):
+        _check(graphs, q, b, srv.poll(t))
+    srv.close()
+
+
+def test_server_admission_by_memory(env):
+    from paper_1607_05707_gb300 import irgl as C
+    from paper_1607_05707_gb300.api import Server
+
+    ctx, graphs, dgs = env
+    big = graphs[0].n  # 16384 vertices
+    # arena of 1.5 large queries: queries queue until memory frees up, all still complete
+    srv = Server(ctx, arena_bytes=int(1.5 * big) * 16, max_slots=8, epoch_rounds=4)
+    qs = [("bfs", 0, int(s)) for s in inputs.sources(graphs[0], 6, seed=9)]
+    bufs = [np.empty(big, dtype=np.uint32) for _ in qs]
+    tickets = [srv.submit(k, dgs[gi], s, b) for (k, gi, s), b in zip(qs, bufs)]
+    # a query that can never fit is rejected at submission
+    huge = inputs.mesh(200, 200, seed=1)
+    dh = ctx.load(huge)
+    with pytest.raises(C.IrglError) as ei:
+        srv.submit("bfs", dh, 0, None)
+    assert ei.value.status == C.IRGL_ERR_ADMISSION
+    srv.drain(120)
+    for q, b, t in zip(qs, bufs, tickets):
+        _check(graphs, q, b, srv.poll(t))
+    st = srv.stats()
+    assert st["completed"] == 6 and st["rejected"] == 1
+    srv.close()
+    dh.close()
+
+
+def test_server_arrivals_while_running(env):
+    """Queries submitted from another thread while earlier ones run join later epochs."""
+    from paper_1607_05707_gb300.api import Server
+
+    ctx, graphs, dgs = env
+    qs = _queries(graphs, 40, seed=8)
+    srv = Server(ctx, arena_bytes=128 << 20, max_slots=16, epoch_rounds=8)
+    bufs = [np.empty(graphs[gi].n, dtype=np.uint32) for _, gi, _ in qs]
+    tickets = [None] * len(qs)
+
+    def feeder():
+        for i, (k, gi, s) in enumerate(qs):
+            tickets[i] = srv.submit(k, dgs[gi], s, bufs[i])
+            time.sleep(0.0005)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    srv.drain(120)
+    infos = [srv.poll(t) for t in tickets]
+    for q, b, info in zip(qs, bufs, infos):
+        _check(graphs, q, b, info)
+    # the queries' work overlapped on the device: the server ran fewer rounds than the
+    # queries were active in total (rounds are shared by every active query)
+    st = srv.stats()
+    assert st["rounds"] < sum(i["rounds"] for i in infos)
+    srv.close()
