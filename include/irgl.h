@@ -321,6 +321,29 @@ irgl_status irgl_server_drain(irgl_server* s, uint32_t timeout_ms);
 irgl_status irgl_server_stats(irgl_server* s, irgl_server_counters* out);
 irgl_status irgl_server_destroy(irgl_server* s);
 
+/* ---------------------------------------------------------------- no-allocation entry point
+ * The paper has no counterpart to this call; it exists for callers that must
+ * not allocate device memory at all: for instance a plugin whose host
+ * application's allocator reserves the whole device at start-up, or a
+ * latency-critical loop that cannot take the implicit device synchronisation
+ * a cudaMalloc may bring. It runs the persistent BFS Iterate from one source
+ * and calls no cudaMalloc, cudaFree or other allocating routine.
+ *   device, cuda_stream: the GPU and the stream (cudaStream_t as void*) to run on
+ *   n, m, row_ptr, col:  the caller's device CSR (as irgl_csr_load; col 16-byte aligned)
+ *   src:                 source vertex, < n
+ *   level:               caller's device array of n uint32 levels (INF = unreachable)
+ *   rounds:              optional host out: Iterate rounds executed
+ * Scratch (status block, two worklists, big list) lives in one file-scope
+ * device array of about 9.6 MiB that every GPU loading the library keeps until
+ * the process exits; n is limited to 1,048,576 vertices (IRGL_ERR_INVALID_ARG
+ * beyond, before any GPU work). Every call shares that array and it keeps the
+ * last call's contents (each call clears its counters), so calls whose GPU work
+ * overlaps race and give wrong results. The first call on a device looks up
+ * the array's address with that device current; make it before any stream
+ * capture. Synchronises on cuda_stream before returning. */
+irgl_status irgl_bfs_noalloc(int device, void* cuda_stream, uint32_t n, uint64_t m, const uint32_t* row_ptr,
+                             const uint32_t* col, uint32_t src, uint32_t* level, uint32_t* rounds);
+
 /* ---------------------------------------------------------------- test hooks
  * Fault injection on the host side only (no device fault is ever raised):
  *   key 1: barrier time limit in microseconds (0 = default 2 s)

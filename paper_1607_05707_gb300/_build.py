@@ -36,6 +36,7 @@ CUDA_UNITS = [
     "irgl_batch.cu",
     "irgl_server.cu",
     "irgl_tune.cu",
+    "irgl_noalloc.cu",
 ]
 HOST_UNITS: list[str] = []
 

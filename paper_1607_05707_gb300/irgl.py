@@ -152,6 +152,7 @@ _SIGS = {
     "irgl_server_destroy": [_P],
     "irgl_autotune": [_P, c_int, _P, _P, c_uint32, c_uint32, POINTER(irgl_tuning), POINTER(ctypes.c_float)],
     "irgl_batch_autotune": [_P, c_uint32, POINTER(irgl_tuning), POINTER(ctypes.c_float)],
+    "irgl_bfs_noalloc": [c_int, _P, c_uint32, c_uint64, _P, _P, c_uint32, _P, POINTER(c_uint32)],
     "irgl_control_cta": [POINTER(c_uint32), c_uint32, c_uint32, POINTER(c_uint32)],
     "irgl_batch_create": [_P, c_uint32, POINTER(_P)],
     "irgl_batch_destroy": [_P],
@@ -469,3 +470,10 @@ def irgl_batch_autotune(b: int, reps: int = 3) -> tuple[dict, float]:
     ms = ctypes.c_float()
     _check(lib().irgl_batch_autotune(b, reps, ctypes.byref(t), ctypes.byref(ms)))
     return t.as_dict(), float(ms.value)
+
+
+def irgl_bfs_noalloc(device: int, cuda_stream: int | None, n: int, m: int, row_ptr: int, col: int, src: int,
+                     level: int) -> int:
+    rounds = c_uint32()
+    _check(lib().irgl_bfs_noalloc(device, cuda_stream, n, m, row_ptr, col, src, level, ctypes.byref(rounds)))
+    return int(rounds.value)
