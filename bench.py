@@ -657,7 +657,8 @@ def run_serve(args, world, rank, local):
                         "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
                         "max_ms": round(1e3 * float(lat.max()), 3)},
             "server": {k: st[k] - base.get(k, 0) if k in ("completed", "epochs", "rounds", "edges") else st[k]
-                       for k in ("completed", "rejected", "epochs", "rounds", "edges", "busy_s", "grid", "cta_size")},
+                       for k in ("completed", "rejected", "epochs", "rounds", "edges", "busy_s", "kernel_s", "grid",
+                                 "cta_size")},
             "verified_against_oracle": len(verify),
             "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 4,
                     "d2h_bytes_per_step": int(4 * np.mean([graphs[g].n for g in gi]))},

@@ -85,6 +85,9 @@ typedef struct {
   uint32_t max_blocks;    /* upper bound on the grid; 0 = none */
   uint32_t flags;         /* IRGL_TUNE_NO_SPLIT: persistent kernels keep long lists in the CTA bin
                              instead of splitting their edges over the whole grid */
+  uint32_t delta;         /* persistent SSSP only: near-far bucket width. Improvements to a distance
+                             >= the current limit wait on a far list until the rounds below the
+                             limit drain; 0 = plain rounds (every improvement is pushed) */
 } irgl_tuning;
 
 #define IRGL_TUNE_NO_SPLIT 0x1u
@@ -303,6 +306,7 @@ typedef struct {
 typedef struct {
   uint64_t submitted, completed, rejected, epochs, rounds, edges;
   double busy_s;      /* worker time spent in epochs */
+  double kernel_s;    /* CUDA-event time of the epoch kernels */
   uint32_t active, queued;
   uint64_t arena_entries;
   uint32_t grid, cta_size;

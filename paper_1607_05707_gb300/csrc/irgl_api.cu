@@ -58,6 +58,7 @@ irgl_tuning default_tuning() {
   t.blocks_per_sm = 0;
   t.max_blocks = 0;
   t.flags = 0;
+  t.delta = 0;
   return t;
 }
 
@@ -71,6 +72,7 @@ irgl_status resolve_tuning(const irgl_tuning* in, irgl_tuning* out) {
     d.blocks_per_sm = in->blocks_per_sm;
     d.max_blocks = in->max_blocks;
     d.flags = in->flags;
+    d.delta = in->delta;
   }
   if (!valid_cta(d.cta_size)) return fail(IRGL_ERR_INVALID_ARG, "cta_size must be 128, 256, 512 or 1024");
   if (d.chunk > 64) return fail(IRGL_ERR_INVALID_ARG, "chunk must be <= 64");
@@ -120,6 +122,7 @@ void reset_status(irgl_ctx* ctx) {
   *ctx->st_host = z;
   cudaMemcpyAsync(ctx->st, ctx->st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, ctx->stream);
   if (ctx->ws_stamp) cudaMemsetAsync(ctx->ws_stamp, 0, sizeof(uint32_t) * (size_t)ctx->ws_stamp_n, ctx->stream);
+  if (ctx->ws_far_stamp) cudaMemsetAsync(ctx->ws_far_stamp, 0, sizeof(uint32_t) * (size_t)ctx->ws_far_n, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
 }
 
@@ -133,7 +136,21 @@ cudaError_t alloc_big(uint32_t cap, uint4** e, unsigned long long** off) {
   return r;
 }
 
-irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp) {
+irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool need_far) {
+  if (need_far && n > ctx->ws_far_n) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws_far[0]);
+    cudaFree(ctx->ws_far[1]);
+    cudaFree(ctx->ws_far_stamp);
+    ctx->ws_far[0] = ctx->ws_far[1] = ctx->ws_far_stamp = nullptr;
+    ctx->ws_far_n = 0;
+    cudaError_t e = cudaMalloc(&ctx->ws_far[0], sizeof(uint32_t) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->ws_far[1], sizeof(uint32_t) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->ws_far_stamp, sizeof(uint32_t) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws_far_stamp, 0, sizeof(uint32_t) * (size_t)n, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "near-far allocation");
+    ctx->ws_far_n = n;
+  }
   const uint32_t bcap = big_capacity(n);
   if (bcap > ctx->big_cap) {
     cudaStreamSynchronize(ctx->stream);
@@ -191,6 +208,7 @@ uint32_t persistent_grid(irgl_ctx* ctx, uint32_t op, const irgl_tuning& t) {
   if (t.blocks_per_sm && static_cast<int>(t.blocks_per_sm) < nb) nb = static_cast<int>(t.blocks_per_sm);
   uint32_t grid = static_cast<uint32_t>(nb) * static_cast<uint32_t>(ctx->sm_count);
   if (t.max_blocks && t.max_blocks < grid) grid = t.max_blocks;
+  grid = std::min<uint32_t>(grid, kMaxGrid);  // one barrier arrival slot per CTA
   return std::max<uint32_t>(grid, 1);
 }
 
@@ -231,6 +249,13 @@ KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tu
   p.trace_cap = ctx->trace_cap;
   p.big = (t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{ctx->big_e, ctx->big_off, ctx->big_cap};
   if (ctx->dbg_big_cap && p.big.cap > ctx->dbg_big_cap) p.big.cap = ctx->dbg_big_cap;
+  if (t.delta && ctx->ws_far_stamp && ctx->ws_far_n >= g->n) {
+    p.far[0] = ctx->ws_far[0];
+    p.far[1] = ctx->ws_far[1];
+    p.far_cap = g->n;
+    p.far_stamp = ctx->ws_far_stamp;
+    p.delta = t.delta;
+  }
   return p;
 }
 
@@ -291,6 +316,9 @@ irgl_status irgl_ctx_destroy(irgl_ctx* ctx) {
   cudaFree(ctx->ws_items[0]);
   cudaFree(ctx->ws_items[1]);
   cudaFree(ctx->ws_stamp);
+  cudaFree(ctx->ws_far[0]);
+  cudaFree(ctx->ws_far[1]);
+  cudaFree(ctx->ws_far_stamp);
   cudaFree(ctx->ws_state);
   cudaFree(ctx->trace);
   cudaFree(ctx->big_e);
@@ -667,7 +695,7 @@ irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workl
   s = resolve_tuning(tin, &t);
   if (s != IRGL_OK) return s;
   DeviceGuard guard(ctx->device);
-  s = ensure_workspace(ctx, g->n, k != IRGL_BFS);
+  s = ensure_workspace(ctx, g->n, k != IRGL_BFS, k == IRGL_SSSP && mode == IRGL_PERSISTENT && t.delta != 0);
   if (s != IRGL_OK) return s;
   const uint32_t op = static_cast<uint32_t>(k);
   KParams p = make_params(ctx, g, state_dev, t);

@@ -301,6 +301,7 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   if (t.blocks_per_sm && static_cast<int>(t.blocks_per_sm) < nb) nb = static_cast<int>(t.blocks_per_sm);
   b->grid = static_cast<uint32_t>(nb) * static_cast<uint32_t>(ctx->sm_count);
   if (t.max_blocks && t.max_blocks < b->grid) b->grid = t.max_blocks;
+  b->grid = std::min<uint32_t>(b->grid, kMaxGrid);
   b->t = t;
   b->bp = BParams{};
   b->bp.desc = b->desc;

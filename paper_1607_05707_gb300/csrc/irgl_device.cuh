@@ -45,9 +45,11 @@ enum : uint32_t {
 };
 
 // Device status block. Each contended family sits on its own 128-byte line.
-// Invariant between launches: arrive, exit_count, tail[], grab[], rel,
+// Invariant between launches: arrive, exit_count, tail[], grab[], rel, qmask,
 // big_ctr, any_true and any_false are 0 (every kernel restores them on a
 // clean exit; the host clears the block after an error).
+constexpr uint32_t kMaxGrid = 2048;  // CTAs of a persistent launch (16-bit arrival count)
+
 struct alignas(128) DevStatus {
   // grid-barrier arrivals of the current barrier: (pushes << 32) | (CTAs that
   // appended to the big list << 16) | arrivals; reset by each barrier's releaser
@@ -76,8 +78,14 @@ struct alignas(128) DevStatus {
   unsigned long long big_ctr;
   unsigned long long big_pub;  // copy published by the barrier's releaser
   uint32_t pad5[28];
+  // per-round bitmaps of the batched queries that pushed (folded into qlast)
+  uint32_t qmask[2][32];
+  // SSSP near-far: sizes of the two far lists and the smallest distance pushed to each
+  uint32_t far_tail[2];
+  uint32_t far_min[2];
+  uint32_t pad6[28];
 };
-static_assert(sizeof(DevStatus) == 768, "status layout");
+static_assert(sizeof(DevStatus) == 1152, "status layout");
 
 // Long adjacency lists of a round (degree >= cta_thresh) are not walked by the
 // CTA that popped them: they go to a grid-wide list and, after a barrier, every
@@ -126,6 +134,11 @@ struct KParams {
   unsigned long long* trace;   // optional per-round trace: {end time ns, (in_n << 32) | out_n}
   uint32_t trace_cap;          // rounds the trace can hold
   BigList big;
+  // SSSP near-far schedule (delta = 0: off)
+  uint32_t* far[2];
+  uint32_t far_cap;
+  uint32_t* far_stamp;
+  uint32_t delta;
 };
 
 // Per-launch (one round) arguments.
@@ -235,6 +248,7 @@ struct Smem {
   uint32_t pub_out;  // out-worklist size published by the grid barrier
   uint32_t pub_err;  // device error code published by the grid barrier
   uint32_t round_pushes;                    // out-worklist slots this CTA reserved in the current round
+  uint32_t far_min_cta;                     // smallest distance this CTA pushed to the far list
   uint32_t big_appended;                    // this CTA appended to the big list in the current round
   uint32_t pub_flags;                       // kRelBigFlag when the big list is pending
   unsigned long long pub_big;               // published big-list counter
@@ -251,6 +265,7 @@ template <int CTA>
 struct BatchSmem {
   Smem<CTA> core;
   uint32_t sbases[kMaxBatchQueries];
+  uint32_t qbits[kMaxBatchQueries / 32];  // queries (by id) this CTA pushed for in the current round
 };
 
 // ----------------------------------------------------------------------------- cooperative-conversion push
@@ -444,7 +459,7 @@ struct BatchView {
   uint32_t nq;
   uint32_t* state;
   uint32_t* stamp;
-  uint32_t* qlast;
+  uint32_t* qbits;  // shared-memory bitmap of queries that pushed this round
   static constexpr bool kBatched = true;
   __device__ __forceinline__ uint32_t op(uint32_t q) const { return __ldg(&desc[q].op); }
   __device__ __forceinline__ const uint32_t* rowp(uint32_t q) const {
@@ -468,7 +483,12 @@ struct BatchView {
     q = lo;
     u = item - sbases[lo];
   }
-  __device__ __forceinline__ void mark(uint32_t q, uint32_t ep) const { qlast[__ldg(&desc[q].slot)] = ep; }
+  // per-instance termination flag: a shared-memory bit per query; the CTA
+  // folds its bits into the round's global bitmap once, before the barrier
+  __device__ __forceinline__ void mark(uint32_t q, uint32_t) const {
+    const uint32_t slot = __ldg(&desc[q].slot);
+    atomicOr(&qbits[slot >> 5], 1u << (slot & 31u));
+  }
 };
 
 // ----------------------------------------------------------------------------- operator
@@ -514,72 +534,6 @@ __device__ __forceinline__ bool needs_w(uint32_t op_rt) {
   return (OP == OP_RUNTIME ? op_rt : OP) == OP_SSSP;
 }
 
-// Edges [beg, end) of one owner, GROUP threads cooperating (GROUP = 32: a warp,
-// GROUP = CTA: the whole CTA); `rank` in [0, GROUP). 16-byte vector loads of
-// col (and w) after an alignment peel; the loop trip count is uniform across
-// the group so the warp-level pushes see converged warps.
-template <uint32_t OP, int CTA, int GROUP, class V>
-__device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Out& out, uint32_t q, uint32_t beg,
-                                            uint32_t end, uint32_t val, uint32_t ep, uint32_t rank) {
-  const uint32_t op = g.op(q);
-  const uint32_t* __restrict__ col = g.colp(q);
-  const int32_t* __restrict__ w = g.wp(q);
-  const uint32_t sb = g.sbase(q);
-  uint32_t* state = g.state + sb;
-  uint32_t* stamp = g.stamp + sb;
-  const bool nw = needs_w<OP>(op);
-  bool any = false;
-  const uint32_t a = min(end, (beg + 3u) & ~3u);
-  const uint32_t b = a + ((end - a) & ~3u);
-  {  // head: up to 3 edges before the 16-byte boundary
-    const uint32_t e = beg + rank;
-    bool p = false;
-    uint32_t v = 0;
-    if (e < a) {
-      v = __ldg(col + e);
-      p = relax<OP>(op, state, stamp, v, val, nw ? __ldg(w + e) : 0, ep);
-    }
-    push1<CTA>(sm, out, p, sb + v);
-    any |= p;
-  }
-  for (uint32_t base = a; base < b; base += 4u * GROUP) {
-    const uint32_t e = base + 4u * rank;
-    uint32_t f = 0;
-    uint4 c = make_uint4(0, 0, 0, 0);
-    if (e < b) {
-      c = __ldg(reinterpret_cast<const uint4*>(col + e));
-      int4 ww = make_int4(0, 0, 0, 0);
-      if (nw) ww = __ldg(reinterpret_cast<const int4*>(w + e));
-      // all four destination loads in flight before any atomic
-      const uint32_t c0 = __ldcg(state + c.x), c1 = __ldcg(state + c.y);
-      const uint32_t c2 = __ldcg(state + c.z), c3 = __ldcg(state + c.w);
-      f |= decide<OP>(op, state, stamp, c.x, val, ww.x, c0, ep) ? 1u : 0u;
-      f |= decide<OP>(op, state, stamp, c.y, val, ww.y, c1, ep) ? 2u : 0u;
-      f |= decide<OP>(op, state, stamp, c.z, val, ww.z, c2, ep) ? 4u : 0u;
-      f |= decide<OP>(op, state, stamp, c.w, val, ww.w, c3, ep) ? 8u : 0u;
-    }
-    push4<CTA>(sm, out, f, sb + c.x, sb + c.y, sb + c.z, sb + c.w);
-    any |= f != 0;
-    if (GROUP == CTA) {
-      // the predicate is taken at the barrier, when every warp's pushes are in
-      if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, out);
-    }
-  }
-  {  // tail: up to 3 edges after the last full vector
-    const uint32_t e = b + rank;
-    bool p = false;
-    uint32_t v = 0;
-    if (e < end) {
-      v = __ldg(col + e);
-      p = relax<OP>(op, state, stamp, v, val, nw ? __ldg(w + e) : 0, ep);
-    }
-    push1<CTA>(sm, out, p, sb + v);
-    any |= p;
-  }
-  if (V::kBatched && any) g.mark(q, ep);  // per-instance termination flag: last round with a push
-  return any;
-}
-
 // ----------------------------------------------------------------------------- one tile of items
 
 struct RoundCtx {
@@ -592,7 +546,122 @@ struct RoundCtx {
   Tune tn;
   BigList big;                    // cap 0: long lists stay in the CTA bin
   unsigned long long* big_ctr;
+  // SSSP near-far: improvements to a distance >= limit go to the far list
+  uint32_t limit;                 // kInf: every improvement goes to `out`
+  Out far_out;
+  uint32_t* far_stamp;
+  uint32_t phase;                 // far-list dedup id of the current phase
 };
+
+// decide() with the SSSP near-far routing: 0 = no push, 1 = push to this
+// round's out-worklist, 2 = push to the far list. Near pushes dedup on the
+// round stamp, far pushes on the phase stamp, so a vertex improved first above
+// and then below the limit within one round still reaches the out-worklist.
+template <uint32_t OP>
+__device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state, uint32_t* stamp, uint32_t v,
+                                                 uint32_t val, int32_t wt, uint32_t cur, const RoundCtx& rc,
+                                                 uint32_t sb, uint32_t& nd_out) {
+  if (OP != OP_SSSP || rc.limit == kInf) return decide<OP>(op_rt, state, stamp, v, val, wt, cur, rc.ep) ? 1u : 0u;
+  const uint32_t nd = val + static_cast<uint32_t>(wt);
+  if (nd >= cur) return 0u;
+  const uint32_t old = atomicMin(state + v, nd);
+  if (nd >= old) return 0u;
+  if (nd < rc.limit) return atomicExch(stamp + v, rc.ep) != rc.ep ? 1u : 0u;
+  nd_out = nd;
+  return atomicExch(rc.far_stamp + sb + v, rc.phase) != rc.phase ? 2u : 0u;
+}
+
+// Far-list pushes: warp-aggregated straight to global memory (rare next to
+// out-worklist pushes), plus the CTA's smallest far distance.
+template <int CTA>
+__device__ __forceinline__ void push_far4(Smem<CTA>& sm, const Out& fo, uint32_t f, uint32_t v0, uint32_t v1,
+                                          uint32_t v2, uint32_t v3, uint32_t dmin) {
+  if (!__any_sync(kFull, f != 0)) return;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t k = __popc(f);
+  const uint32_t incl = warp_incl_scan(k);
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  uint32_t gb = 0;
+  if (lane == 31) gb = atomicAdd(fo.tail, total);
+  gb = __shfl_sync(kFull, gb, 31);
+  uint32_t pos = gb + incl - k;
+  const uint32_t vs[4] = {v0, v1, v2, v3};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (f >> i & 1u) {
+      if (pos < fo.cap) __stcg(fo.items + pos, vs[i]);
+      else set_err(fo.err, DERR_WL_OVERFLOW);
+      ++pos;
+    }
+  }
+  if (f) atomicMin(&sm.far_min_cta, dmin);
+}
+
+// Edges [beg, end) of one owner, GROUP threads cooperating (GROUP = 32: a warp,
+// GROUP = CTA: the whole CTA); `rank` in [0, GROUP). 16-byte vector loads of
+// col (and w) after an alignment peel; the loop trip count is uniform across
+// the group so the warp-level pushes see converged warps.
+template <uint32_t OP, int CTA, int GROUP, class V>
+__device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const RoundCtx& rc, uint32_t q, uint32_t beg,
+                                            uint32_t end, uint32_t val, uint32_t rank) {
+  const uint32_t op = g.op(q);
+  const uint32_t* __restrict__ col = g.colp(q);
+  const int32_t* __restrict__ w = g.wp(q);
+  const uint32_t sb = g.sbase(q);
+  uint32_t* state = g.state + sb;
+  uint32_t* stamp = g.stamp + sb;
+  const bool nw = needs_w<OP>(op);
+  bool any = false;
+  const uint32_t a = min(end, (beg + 3u) & ~3u);
+  const uint32_t b = a + ((end - a) & ~3u);
+  // head (edges before the 16-byte boundary) and tail (after the last full vector): scalar
+  auto scalar = [&](uint32_t e, uint32_t lim) {
+    uint32_t r = 0, v = 0, nd = 0;
+    if (e < lim) {
+      v = __ldg(col + e);
+      const int32_t wt = nw ? __ldg(w + e) : 0;
+      r = decide_route<OP>(op, state, stamp, v, val, wt, __ldcg(state + v), rc, sb, nd);
+    }
+    push1<CTA>(sm, rc.out, r == 1u, sb + v);
+    if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, r == 2u ? 1u : 0u, sb + v, 0u, 0u, 0u, nd);
+    any |= r != 0;
+  };
+  scalar(beg + rank, a);
+  for (uint32_t base = a; base < b; base += 4u * GROUP) {
+    const uint32_t e = base + 4u * rank;
+    uint32_t fn = 0, ff = 0, dmin = kInf;
+    uint4 c = make_uint4(0, 0, 0, 0);
+    if (e < b) {
+      c = __ldg(reinterpret_cast<const uint4*>(col + e));
+      int4 ww = make_int4(0, 0, 0, 0);
+      if (nw) ww = __ldg(reinterpret_cast<const int4*>(w + e));
+      // all four destination loads in flight before any atomic
+      const uint32_t c0 = __ldcg(state + c.x), c1 = __ldcg(state + c.y);
+      const uint32_t c2 = __ldcg(state + c.z), c3 = __ldcg(state + c.w);
+      uint32_t nd0 = 0, nd1 = 0, nd2 = 0, nd3 = 0;
+      const uint32_t r0 = decide_route<OP>(op, state, stamp, c.x, val, ww.x, c0, rc, sb, nd0);
+      const uint32_t r1 = decide_route<OP>(op, state, stamp, c.y, val, ww.y, c1, rc, sb, nd1);
+      const uint32_t r2 = decide_route<OP>(op, state, stamp, c.z, val, ww.z, c2, rc, sb, nd2);
+      const uint32_t r3 = decide_route<OP>(op, state, stamp, c.w, val, ww.w, c3, rc, sb, nd3);
+      fn = (r0 == 1u ? 1u : 0u) | (r1 == 1u ? 2u : 0u) | (r2 == 1u ? 4u : 0u) | (r3 == 1u ? 8u : 0u);
+      if (OP == OP_SSSP) {
+        ff = (r0 == 2u ? 1u : 0u) | (r1 == 2u ? 2u : 0u) | (r2 == 2u ? 4u : 0u) | (r3 == 2u ? 8u : 0u);
+        dmin = min(min(r0 == 2u ? nd0 : kInf, r1 == 2u ? nd1 : kInf), min(r2 == 2u ? nd2 : kInf, r3 == 2u ? nd3 : kInf));
+      }
+    }
+    push4<CTA>(sm, rc.out, fn, sb + c.x, sb + c.y, sb + c.z, sb + c.w);
+    if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, ff, sb + c.x, sb + c.y, sb + c.z, sb + c.w, dmin);
+    any |= (fn | ff) != 0;
+    if (GROUP == CTA) {
+      // the predicate is taken at the barrier, when every warp's pushes are in
+      if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
+    }
+  }
+  scalar(b + rank, end);
+  if (V::kBatched && any) g.mark(q, rc.ep);  // per-instance termination flag
+  return any;
+}
+
 
 template <uint32_t OP, int CTA, int RED, class V>
 __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const RoundCtx& rc, uint32_t idx,
@@ -664,7 +733,7 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
       big = false;
     }
     __syncthreads();
-    const bool p = group_edges<OP, CTA, CTA>(g, sm, rc.out, sm.own_q, sm.own_beg, sm.own_end, sm.own_val, rc.ep, tid);
+    const bool p = group_edges<OP, CTA, CTA>(g, sm, rc, sm.own_q, sm.own_beg, sm.own_end, sm.own_val, tid);
     if (RED == RED_ALL && p) sm.pushed[sm.own_tid] = 1;
     pushed |= p;
   }
@@ -680,7 +749,7 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
     const uint32_t wv = __shfl_sync(kFull, val, ld);
     const uint32_t wq = __shfl_sync(kFull, q, ld);
     if (lane == static_cast<uint32_t>(ld)) mid = false;
-    const bool p = group_edges<OP, CTA, 32>(g, sm, rc.out, wq, wb, we, wv, rc.ep, lane);
+    const bool p = group_edges<OP, CTA, 32>(g, sm, rc, wq, wb, we, wv, lane);
     if (RED == RED_ALL && p) sm.pushed[(tid & ~31u) + ld] = 1;
     pushed |= p;
   }
@@ -731,18 +800,27 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
       }
 #pragma unroll
       for (uint32_t k = 0; k < E; ++k) cur[k] = (base + k * CTA + tid < total) ? __ldcg(g.state + sb[k] + v[k]) : 0u;
-      uint32_t f = 0;
+      uint32_t f = 0, ff = 0, dmin = kInf;
 #pragma unroll
       for (uint32_t k = 0; k < E; ++k) {
-        if (base + k * CTA + tid < total &&
-            decide<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], sm.s_val[own[k]], wt[k], cur[k], rc.ep)) {
-          f |= 1u << k;
+        uint32_t nd = 0;
+        const uint32_t r = base + k * CTA + tid < total
+                               ? decide_route<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], sm.s_val[own[k]], wt[k],
+                                                  cur[k], rc, sb[k], nd)
+                               : 0u;
+        if (r == 1u) f |= 1u << k;
+        if (r == 2u) {
+          ff |= 1u << k;
+          dmin = min(dmin, nd);
+        }
+        if (r != 0u) {
           if (RED == RED_ALL) sm.pushed[own[k]] = 1;
           if (V::kBatched) g.mark(sm.s_q[own[k]], rc.ep);
         }
       }
       push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
-      pushed |= f != 0;
+      if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, ff, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3], dmin);
+      pushed |= (f | ff) != 0;
       if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
     }
   }
@@ -787,6 +865,12 @@ __device__ __forceinline__ void round_body(const V& g, Smem<CTA>& sm, const Roun
 __device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -957,18 +1041,24 @@ __device__ __forceinline__ void big_phase(const V& g, Smem<CTA>& sm, const Round
         }
 #pragma unroll
         for (uint32_t k = 0; k < E; ++k) cur[k] = (base + k * CTA + tid < wend) ? __ldcg(g.state + sb[k] + v[k]) : 0u;
-        uint32_t f = 0;
+        uint32_t f = 0, ff = 0, dmin = kInf;
 #pragma unroll
         for (uint32_t k = 0; k < E; ++k) {
           if (base + k * CTA + tid < wend) {
             const uint4 en = sm.be[own[k]];
-            if (decide<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], en.z, wt[k], cur[k], rc.ep)) {
-              f |= 1u << k;
-              if (V::kBatched) g.mark(en.w, rc.ep);
+            uint32_t nd = 0;
+            const uint32_t r =
+                decide_route<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], en.z, wt[k], cur[k], rc, sb[k], nd);
+            if (r == 1u) f |= 1u << k;
+            if (r == 2u) {
+              ff |= 1u << k;
+              dmin = min(dmin, nd);
             }
+            if (V::kBatched && r != 0u) g.mark(en.w, rc.ep);
           }
         }
         push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
+        if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, ff, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3], dmin);
         if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
       }
       pos = wend;
@@ -1004,6 +1094,32 @@ __device__ __forceinline__ void init_smem(Smem<CTA>& sm) {
   __syncthreads();
 }
 
+// SSSP near-far phase change: every item of the finished phase's far list is
+// checked against its current distance d. d < lim_old: it was improved below
+// the old limit after it was pushed far, which pushed it to an out-worklist
+// then, so it is dropped. lim_old <= d < lim_new: it joins this round's
+// out-worklist. d >= lim_new: it stays far, in the other far list.
+template <uint32_t OP, int CTA, class V>
+__device__ __forceinline__ void split_far(const V& g, Smem<CTA>& sm, const RoundCtx& rc, const uint32_t* fin,
+                                          uint32_t far_n, uint32_t lim_old, uint32_t lim_new) {
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t base = blockIdx.x * CTA; base < far_n; base += gridDim.x * CTA) {
+    const uint32_t i = base + tid;
+    uint32_t v = 0, d = kInf;
+    if (i < far_n) {
+      v = __ldcg(fin + i);
+      d = __ldcg(g.state + v);
+    }
+    const bool near = i < far_n && d >= lim_old && d < lim_new && atomicExch(g.stamp + v, rc.ep) != rc.ep;
+    const bool keep = i < far_n && d >= lim_new && atomicExch(rc.far_stamp + v, rc.phase) != rc.phase;
+    push1<CTA>(sm, rc.out, near, v);
+    push_far4<CTA>(sm, rc.far_out, keep ? 1u : 0u, v, 0u, 0u, 0u, d);
+    if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
+  }
+  __syncthreads();
+  flush_stage<CTA>(sm, rc.out);
+}
+
 // ----------------------------------------------------------------------------- state initialisation
 
 // Iterate initial values (Initial[...] of the BFS listing): BFS/SSSP state = INF
@@ -1037,17 +1153,26 @@ __device__ __forceinline__ void fill_state(uint32_t* state, uint32_t n, const ui
 // ----------------------------------------------------------------------------- kernels
 
 // Clean exit of a persistent launch: the last CTA out restores the
-// between-launch invariants (counters at 0) and publishes the outcome.
+// between-launch invariants (counters, release word and arrival slots at 0)
+// and publishes the outcome. Called by every thread of every CTA.
 template <int CTA>
-__device__ __forceinline__ void persistent_exit(DevStatus* st, bool ok, uint32_t rounds, uint32_t last_out, uint32_t ep0,
-                                                unsigned long long esum, uint32_t* cont, uint32_t cont_buf) {
-  if (threadIdx.x != 0) return;
-  atomicAdd(&st->edges, esum);
-  if (!ok) return;
+__device__ __forceinline__ void persistent_exit(Smem<CTA>& sm, DevStatus* st, bool ok, uint32_t rounds,
+                                                uint32_t last_out, uint32_t ep0, unsigned long long esum,
+                                                uint32_t* cont, uint32_t cont_buf) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&st->edges, esum);
+    uint32_t last = 0;
+    if (ok) {
+      __threadfence();
+      last = atomicAdd(&st->exit_count, 1u) == gridDim.x - 1 ? 1u : 0u;
+    }
+    sm.flag = last;
+  }
+  __syncthreads();
+  if (sm.flag == 0) return;
   __threadfence();
-  const uint32_t prev = atomicAdd(&st->exit_count, 1u);
-  if (prev == gridDim.x - 1) {
-    __threadfence();
+  if (threadIdx.x == 0) {
     if (cont) {
       cont[0] = cont_buf;
       cont[1] = last_out;
@@ -1062,9 +1187,11 @@ __device__ __forceinline__ void persistent_exit(DevStatus* st, bool ok, uint32_t
     st->arrive = 0;
     st->rel = 0;
     st->big_ctr = 0;
+    st->far_tail[0] = st->far_tail[1] = 0;
+    st->far_min[0] = st->far_min[1] = 0;
     st->exit_count = 0;
-    __threadfence();
   }
+  __threadfence();
 }
 
 __device__ __forceinline__ void trace_round(unsigned long long* trace, uint32_t cap, uint32_t r, uint32_t in_n,
@@ -1111,6 +1238,15 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   if (ok) ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
   trace_round(p.trace, p.trace_cap, 0, init_n, 0);
 
+  // SSSP near-far schedule: improvements to a distance >= limit wait on a far
+  // list; when a round pushes nothing below the limit, a split round raises the
+  // limit and releases the far items below it (delta = 0: plain rounds).
+  const bool nf = OP == OP_SSSP && p.delta != 0 && p.far_stamp != nullptr;
+  uint32_t limit = nf ? p.delta : kInf, lim_old = 0;
+  uint32_t fb = 0;        // far list receiving pushes in the current phase
+  uint32_t phase = ep0;   // far-list dedup id of the current phase
+  uint32_t far_n = 0;
+  bool split = false;
   uint32_t in_n = init_n;
   for (uint32_t r = 0; ok; ++r) {
     uint32_t* const cur = (r & 1) ? p.items[1] : p.items[0];  // no dynamic index into the param struct
@@ -1125,6 +1261,11 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     rc.tn = p.tn;
     rc.big = p.big;
     rc.big_ctr = &st->big_ctr;
+    rc.limit = limit;
+    rc.far_stamp = p.far_stamp;
+    rc.phase = phase;
+    const uint32_t ftarget = split ? (fb ^ 1u) : fb;  // far list this round pushes to
+    rc.far_out = Out{ftarget ? p.far[1] : p.far[0], &st->far_tail[ftarget], p.far_cap, &st->err};
     if (threadIdx.x == 0) {
       if (blockIdx.x == 0) {
         st->tail[(r + 2) % 3] = 0;
@@ -1132,19 +1273,55 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
       }
       sm.round_pushes = 0;
       sm.big_appended = 0;
+      sm.far_min_cta = kInf;
     }
-    round_body<OP, CTA, RED_NONE>(g, sm, rc, edges, dummy_t, dummy_f);
-    ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns, p.big.cap != 0);
+    if (split) {
+      split_far<OP, CTA>(g, sm, rc, fb ? p.far[1] : p.far[0], far_n, lim_old, limit);
+    } else {
+      round_body<OP, CTA, RED_NONE>(g, sm, rc, edges, dummy_t, dummy_f);
+    }
+    if (nf && threadIdx.x == 0 && sm.far_min_cta != kInf) atomicMax(&st->far_min[ftarget], ~sm.far_min_cta);
+    ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns, !split && p.big.cap != 0);
     if (!ok) break;
     if (sm.pub_flags & kRelBigFlag) {
       big_phase<OP, CTA>(g, sm, rc, sm.pub_big);
+      if (nf && threadIdx.x == 0 && sm.far_min_cta != kInf) atomicMax(&st->far_min[ftarget], ~sm.far_min_cta);
       ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
       if (!ok) break;
     }
     last_out = sm.pub_out;
     rounds = r + 1;
     trace_round(p.trace, p.trace_cap, rounds, in_n, last_out);
-    if (last_out == 0 || sm.pub_err != DERR_NONE) break;
+    if (sm.pub_err != DERR_NONE) break;
+    if (split) {
+      // the split list is consumed: clear it for a later phase, continue with the kept list
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->far_tail[fb] = 0;
+        st->far_min[fb] = 0;
+      }
+      fb ^= 1u;
+      split = false;
+    }
+    if (last_out == 0) {
+      if (!nf) break;
+      if (threadIdx.x == 0) {
+        sm.gbase = __ldcg(&st->far_tail[fb]);
+        sm.own_val = ~__ldcg(&st->far_min[fb]);
+      }
+      __syncthreads();
+      far_n = min(sm.gbase, p.far_cap);
+      const uint32_t fmin = sm.own_val;
+      __syncthreads();
+      if (far_n == 0) break;
+      // next phase: at least one delta higher, and high enough to release the nearest far item
+      const unsigned long long l1 = static_cast<unsigned long long>(limit) + p.delta;
+      const unsigned long long l2 = (static_cast<unsigned long long>(fmin) / p.delta + 1ull) * p.delta;
+      const unsigned long long ln = l1 > l2 ? l1 : l2;
+      lim_old = limit;
+      limit = ln >= kInf ? kInf : static_cast<uint32_t>(ln);
+      phase = ep0 + r + 1;  // the split round's id
+      split = true;
+    }
     if (rounds >= p.max_rounds) {
       if (blockIdx.x == 0 && threadIdx.x == 0) set_err(&st->err, DERR_MAX_ROUNDS);
       break;
@@ -1152,7 +1329,7 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     in_n = min(last_out, p.cap);
   }
   const unsigned long long esum = cta_sum_u64<CTA>(sm, edges);
-  persistent_exit<CTA>(st, ok, rounds, last_out, ep0, esum, nullptr, 0);
+  persistent_exit<CTA>(sm, st, ok, rounds, last_out, ep0, esum, nullptr, 0);
 }
 
 // One invocation (Invoke, or one round of a per-launch Iterate).
@@ -1172,6 +1349,10 @@ __device__ __forceinline__ void invoke_round(const KParams& p, const RoundArgs& 
   rc.tn = p.tn;
   rc.big = BigList{nullptr, nullptr, 0};  // one launch, no grid barrier: long lists stay in the CTA bin
   rc.big_ctr = nullptr;
+  rc.limit = kInf;
+  rc.far_out = Out{nullptr, nullptr, 0, &st->err};
+  rc.far_stamp = nullptr;
+  rc.phase = 0;
   uint32_t edges = 0, any_true = 0, any_false = 0;
   round_body<OP, CTA, RED>(g, sm, rc, edges, any_true, any_false);
   const int t = __syncthreads_or(any_true != 0);
@@ -1214,7 +1395,34 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
   const uint32_t ep0 = __ldcg(&st->epoch);
   const uint32_t cur0 = __ldcg(p.cont) & 1u;
   const uint32_t init_n = nq == 0 ? 0u : min(__ldcg(p.cont + 1), p.cap);
-  BatchView g{p.desc, bs.sbases, nq, p.state, p.stamp, p.qlast};
+  BatchView g{p.desc, bs.sbases, nq, p.state, p.stamp, bs.qbits};
+  if (threadIdx.x < kMaxBatchQueries / 32) bs.qbits[threadIdx.x] = 0;
+  __syncthreads();
+  // fold this CTA's query bits into the round's global bitmap (before a barrier)
+  auto fold_marks = [&](uint32_t r) {
+    __syncthreads();
+    for (uint32_t w = threadIdx.x; w < kMaxBatchQueries / 32; w += CTA) {
+      const uint32_t bits = bs.qbits[w];
+      if (bits) {
+        atomicOr(&st->qmask[r & 1][w], bits);
+        bs.qbits[w] = 0;
+      }
+    }
+  };
+  // after round r's last barrier: CTA 0 turns the round's bitmap into qlast stamps
+  auto publish_marks = [&](uint32_t r, uint32_t ep) {
+    if (blockIdx.x != 0) return;
+    for (uint32_t w = threadIdx.x; w < kMaxBatchQueries / 32; w += CTA) {
+      uint32_t bits = __ldcg(&st->qmask[r & 1][w]);
+      if (!bits) continue;
+      st->qmask[r & 1][w] = 0;
+      while (bits) {
+        const uint32_t b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        p.qlast[w * 32 + b] = ep;
+      }
+    }
+  };
   uint32_t edges = 0, dummy_t = 0, dummy_f = 0, rounds = 0, last_out = 0;
   bool ok = true;
   trace_round(p.trace, p.trace_cap, 0, init_n, 0);
@@ -1231,6 +1439,10 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
     rc.tn = p.tn;
     rc.big = p.big;
     rc.big_ctr = &st->big_ctr;
+    rc.limit = kInf;
+    rc.far_out = Out{nullptr, nullptr, 0, &st->err};
+    rc.far_stamp = nullptr;
+    rc.phase = 0;
     if (threadIdx.x == 0) {
       if (blockIdx.x == 0) {
         st->tail[(r + 2) % 3] = 0;
@@ -1240,13 +1452,16 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
       sm.big_appended = 0;
     }
     round_body<OP_RUNTIME, CTA, RED_NONE>(g, sm, rc, edges, dummy_t, dummy_f);
+    fold_marks(r);
     ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns, p.big.cap != 0);
     if (!ok) break;
     if (sm.pub_flags & kRelBigFlag) {
       big_phase<OP_RUNTIME, CTA>(g, sm, rc, sm.pub_big);
+      fold_marks(r);
       ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
       if (!ok) break;
     }
+    publish_marks(r, rc.ep);
     last_out = sm.pub_out;
     rounds = r + 1;
     trace_round(p.trace, p.trace_cap, rounds, in_n, last_out);
@@ -1258,7 +1473,7 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
     in_n = min(last_out, p.cap);
   }
   const unsigned long long esum = cta_sum_u64<CTA>(sm, edges);
-  persistent_exit<CTA>(st, ok, rounds, last_out, ep0, esum, p.cont, (cur0 + rounds) & 1u);
+  persistent_exit<CTA>(sm, st, ok, rounds, last_out, ep0, esum, p.cont, (cur0 + rounds) & 1u);
 }
 
 // Admission of new queries into a batch: per new query j, arena range

@@ -24,6 +24,9 @@ struct irgl_ctx {
   uint4* big_e = nullptr;               // big list of long adjacency lists (persistent kernels)
   unsigned long long* big_off = nullptr;
   uint32_t big_cap = 0;
+  uint32_t* ws_far[2] = {nullptr, nullptr};  // SSSP near-far lists
+  uint32_t* ws_far_stamp = nullptr;
+  uint32_t ws_far_n = 0;
   uint32_t* ws_stamp = nullptr;  // SSSP/CC push dedup stamps
   uint32_t ws_stamp_n = 0;
   uint32_t* ws_state = nullptr;  // result buffer of irgl_run with a host output
@@ -76,14 +79,15 @@ irgl_tuning default_tuning();
 irgl_status resolve_tuning(const irgl_tuning* in, irgl_tuning* out);
 irgl_status read_status(irgl_ctx* ctx, DevStatus* out);
 void reset_status(irgl_ctx* ctx);
-irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp);
+irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool need_far = false);
 uint32_t big_capacity(uint64_t n);
 cudaError_t alloc_big(uint32_t cap, uint4** e, unsigned long long** off);
 int occupancy(irgl_ctx* ctx, int kind, uint32_t op, uint32_t cta, int red);
 uint32_t persistent_grid(irgl_ctx* ctx, uint32_t op, const irgl_tuning& t);
 irgl_status check_kernel_graph(irgl_kernel k, const irgl_graph* g);
 KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tuning& t);
-irgl_status tune_descend(const std::function<float(const irgl_tuning&)>& measure, irgl_tuning* best, float* best_ms);
+irgl_status tune_descend(const std::function<float(const irgl_tuning&)>& measure, irgl_tuning* best, float* best_ms,
+                         bool with_delta = false);
 
 }  // namespace irgl
 

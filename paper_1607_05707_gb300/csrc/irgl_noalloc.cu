@@ -18,6 +18,7 @@
 // The first call on a device looks up the array's device address (with that
 // device current) and caches it; make that first call before any stream
 // capture.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -41,7 +42,7 @@ struct NoAllocScratch {
   unsigned long long big_off[kNoAllocBigCap];
 };
 
-// 768 B status + 128 B + 8 MiB worklists + 1.5 MiB big list: about 9.6 MiB per device.
+// about 17 KiB status + 128 B + 8 MiB worklists + 1.5 MiB big list: about 9.6 MiB per device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
 __global__ void __launch_bounds__(kNoAllocCta, MinBlocks<kNoAllocCta>::value) k_bfs_noalloc(KParams p) {
@@ -72,7 +73,7 @@ irgl_status setup_device(int device, DeviceSetup* out) {
     if (e != cudaSuccess) return cuda_fail(e, "no-alloc launch set-up");
     if (nb <= 0) return fail(IRGL_ERR_CUDA, "no-alloc kernel cannot be made resident");
     d.scratch = static_cast<NoAllocScratch*>(ptr);
-    d.grid = static_cast<uint32_t>(nb) * static_cast<uint32_t>(sms);
+    d.grid = std::min<uint32_t>(static_cast<uint32_t>(nb) * static_cast<uint32_t>(sms), kMaxGrid);
     d.ready = true;
   }
   *out = d;

@@ -168,6 +168,8 @@ struct irgl_server {
   uint64_t submitted = 0, completed = 0, rejected = 0, epochs = 0, rounds_total = 0;
   uint64_t edges_total = 0;
   double busy_s = 0;
+  double kernel_s = 0;  // CUDA-event time of the epoch kernels
+  cudaEvent_t ev[2] = {nullptr, nullptr};
   int32_t fatal = IRGL_OK;
   bool stop = false;
   std::thread worker;
@@ -198,6 +200,8 @@ void server_free(irgl_server* s) {
   if (s->h_qlast) cudaFreeHost(s->h_qlast);
   if (s->h_edges) cudaFreeHost(s->h_edges);
   if (s->h_scratch) cudaFreeHost(s->h_scratch);
+  if (s->ev[0]) cudaEventDestroy(s->ev[0]);
+  if (s->ev[1]) cudaEventDestroy(s->ev[1]);
   if (s->stream) cudaStreamDestroy(s->stream);
 }
 
@@ -285,7 +289,9 @@ bool server_step(irgl_server* s) {
   bp.rounds_cap_is_error = 0;
   bp.timeout_ns = 2000000000ull;
   bp.big = (s->t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{s->big_e, s->big_off, s->big_cap};
+  if (e == cudaSuccess && nq) e = cudaEventRecord(s->ev[0], s->stream);
   if (e == cudaSuccess && nq) e = launch_batch_iterate(s->t.cta_size, s->grid, bp, s->stream);
+  if (e == cudaSuccess && nq) e = cudaEventRecord(s->ev[1], s->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s->st_host, s->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess && nq) e = cudaMemcpyAsync(s->h_qlast, s->qlast, sizeof(uint32_t) * max_slots,
@@ -300,6 +306,11 @@ bool server_step(irgl_server* s) {
     return false;
   }
   const uint32_t rounds = s->st_host->rounds;
+  float kms = 0.f;
+  if (nq && cudaEventElapsedTime(&kms, s->ev[0], s->ev[1]) == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->kernel_s += kms * 1e-3;
+  }
   const uint32_t last_ep = s->st_host->epoch - 1;  // round id of the epoch's last round
   // finished queries: no push in the last round
   std::vector<Active> keep, fin;
@@ -400,6 +411,8 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   s->arena_n = std::min<uint64_t>(bytes / 16, 0xFFFFFFF0ull);
   const uint32_t S = cfg->max_slots;
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev[1]);
   if (e == cudaSuccess) e = cudaMalloc(&s->st, sizeof(DevStatus));
   if (e == cudaSuccess) e = cudaMallocHost(&s->st_host, sizeof(DevStatus));
   if (e == cudaSuccess) e = cudaMalloc(&s->state, sizeof(uint32_t) * s->arena_n);
@@ -447,6 +460,7 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   if (t.blocks_per_sm && static_cast<int>(t.blocks_per_sm) < nb) nb = static_cast<int>(t.blocks_per_sm);
   s->grid = static_cast<uint32_t>(nb) * static_cast<uint32_t>(ctx->sm_count);
   if (t.max_blocks && t.max_blocks < s->grid) s->grid = t.max_blocks;
+  s->grid = std::min<uint32_t>(s->grid, kMaxGrid);
   s->arena.init(s->arena_n);
   for (uint32_t i = 0; i < S; ++i) s->free_slots.push_back(S - 1 - i);
   s->worker = std::thread(server_loop, s);
@@ -520,6 +534,7 @@ irgl_status irgl_server_stats(irgl_server* s, irgl_server_counters* out) {
   out->rounds = s->rounds_total;
   out->edges = s->edges_total;
   out->busy_s = s->busy_s;
+  out->kernel_s = s->kernel_s;
   out->active = static_cast<uint32_t>(s->active.size());
   out->queued = static_cast<uint32_t>(s->queue.size());
   out->arena_entries = s->arena_n;

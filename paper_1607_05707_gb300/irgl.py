@@ -52,6 +52,7 @@ class irgl_tuning(ctypes.Structure):
         ("blocks_per_sm", c_uint32),
         ("max_blocks", c_uint32),
         ("flags", c_uint32),
+        ("delta", c_uint32),
     ]
 
     def as_dict(self) -> dict:
@@ -100,12 +101,14 @@ class irgl_query_info(ctypes.Structure):
 class irgl_server_counters(ctypes.Structure):
     _fields_ = [
         ("submitted", c_uint64), ("completed", c_uint64), ("rejected", c_uint64), ("epochs", c_uint64),
-        ("rounds", c_uint64), ("edges", c_uint64), ("busy_s", ctypes.c_double), ("active", c_uint32),
+        ("rounds", c_uint64), ("edges", c_uint64), ("busy_s", ctypes.c_double), ("kernel_s", ctypes.c_double),
+        ("active", c_uint32),
         ("queued", c_uint32), ("arena_entries", c_uint64), ("grid", c_uint32), ("cta_size", c_uint32),
     ]
 
     def as_dict(self) -> dict:
-        return {k: (float(getattr(self, k)) if k == "busy_s" else int(getattr(self, k))) for k, _ in self._fields_}
+        return {k: (float(getattr(self, k)) if k in ("busy_s", "kernel_s") else int(getattr(self, k)))
+                for k, _ in self._fields_}
 
 
 class IrglError(RuntimeError):

@@ -27,6 +27,9 @@ SCHEDULES = [
     dict(cta_size=128, warp_thresh=16, cta_thresh=512, max_blocks=1),
     dict(cta_size=256, warp_thresh=32, cta_thresh=256, flags=1),  # long lists kept in the CTA bin (no split)
     dict(cta_size=1024, warp_thresh=2, cta_thresh=8),             # most lists split over the grid
+    dict(cta_size=128, delta=16),                                 # SSSP near-far schedule
+    dict(cta_size=256, warp_thresh=4, cta_thresh=16, delta=1),    # near-far, one distance per bucket
+    dict(cta_size=512, delta=100000),                             # near-far bucket wider than any distance
 ]
 
 
