@@ -50,7 +50,8 @@ typedef int irgl_status;
 typedef enum {
   IRGL_BFS = 0,  /* level assignment, Sec. 4.1 level-by-level BFS listing */
   IRGL_SSSP = 1, /* data-driven edge relaxation with atomicMin */
-  IRGL_CC = 2    /* min-label propagation over a symmetric graph */
+  IRGL_CC = 2,   /* min-label propagation over a symmetric graph */
+  IRGL_CC_JUMP = 3 /* same labels by min-hooking and pointer jumping (persistent Iterate only) */
 } irgl_kernel;
 
 /* How Iterate drives the kernel (Sec. 4.4 kernel invocations). */
@@ -67,6 +68,8 @@ typedef enum { IRGL_REDUCE_ANY = 0, IRGL_REDUCE_ALL = 1 } irgl_reduce;
 #define IRGL_DEVICE_PTRS 0x1 /* device arrays: borrowed, must outlive the graph, 16-byte aligned */
 #define IRGL_SYMMETRIC 0x2   /* every edge (u,v) has its reverse (v,u); required by CC */
 #define IRGL_VALIDATE 0x4    /* full host validation (always done for host pointers) */
+#define IRGL_IN_EDGES 0x8    /* host pointers only: also build and upload the in-edge CSR (transpose),
+                                which direction-optimising BFS needs on a non-symmetric graph */
 
 typedef struct irgl_ctx irgl_ctx;
 typedef struct irgl_graph irgl_graph;
@@ -91,6 +94,9 @@ typedef struct {
 } irgl_tuning;
 
 #define IRGL_TUNE_NO_SPLIT 0x1u
+#define IRGL_TUNE_DIROPT 0x2u /* persistent BFS: rounds with a large frontier run bottom-up (every
+                                 unvisited vertex looks for a parent among its in-edges); needs a
+                                 symmetric graph or one loaded with IRGL_IN_EDGES, else ignored */
 
 /* Per-call counters. */
 typedef struct {
@@ -356,7 +362,8 @@ irgl_status irgl_bfs_noalloc(int device, void* cuda_stream, uint32_t n, uint64_t
  *          IRGL_ERR_BARRIER_TIMEOUT.
  *   key 3: override the capacity of the Iterate scratch worklists (0 = n).
  *   key 4: cap the big list of persistent Iterate launches (0 = default), so
- *          long lists beyond the cap take the CTA-bin path. */
+ *          long lists beyond the cap take the CTA-bin path.
+ *   key 5: 1 = direction-optimising BFS runs every round bottom-up. */
 irgl_status irgl_debug_set(irgl_ctx* ctx, int key, int64_t value);
 
 #ifdef __cplusplus

@@ -95,7 +95,7 @@ def build_irgl(force: bool = False, extra_flags: list[str] | None = None) -> Pat
         "-I",
         str(CSRC),
         "--expt-relaxed-constexpr",
-    ] + (extra_flags or [])
+    ] + (extra_flags or []) + os.environ.get("IRGL_EXTRA_NVCC_FLAGS", "").split()
     if os.environ.get("IRGL_PTXAS_VERBOSE"):
         flags += ["-Xptxas", "-v"]
     objs: list[Path] = []

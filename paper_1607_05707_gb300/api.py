@@ -19,11 +19,14 @@ def _np_ptr(a: np.ndarray | None) -> int | None:
 class Graph:
     """A CSR graph resident on the device (owned by the library)."""
 
-    def __init__(self, ctx: "Context", g: CSR, symmetric: bool | None = None, validate: bool = True):
+    def __init__(self, ctx: "Context", g: CSR, symmetric: bool | None = None, validate: bool = True,
+                 in_edges: bool = False):
         self.ctx = ctx
         self.n, self.m = g.n, g.m
         self.symmetric = g.symmetric if symmetric is None else symmetric
         flags = C.IRGL_HOST_PTRS | (C.IRGL_SYMMETRIC if self.symmetric else 0) | (C.IRGL_VALIDATE if validate else 0)
+        if in_edges:
+            flags |= C.IRGL_IN_EDGES
         rp = np.ascontiguousarray(g.row_ptr, dtype=np.uint32)
         col = np.ascontiguousarray(g.col, dtype=np.uint32)
         w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.int32)
@@ -87,8 +90,8 @@ class Context:
         self.handle = C.irgl_ctx_create(device, self.stream.cuda_stream)
         self.sm_count, self.default_tuning = C.irgl_ctx_info(self.handle)
 
-    def load(self, g: CSR, symmetric: bool | None = None, validate: bool = True) -> Graph:
-        return Graph(self, g, symmetric, validate)
+    def load(self, g: CSR, symmetric: bool | None = None, validate: bool = True, in_edges: bool = False) -> Graph:
+        return Graph(self, g, symmetric, validate, in_edges)
 
     def worklist(self, capacity: int) -> Worklist:
         return Worklist(self, capacity)

@@ -192,7 +192,7 @@ irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool ne
 }
 
 int occupancy(irgl_ctx* ctx, int kind, uint32_t op, uint32_t cta, int red) {
-  const int key = ((kind * 4 + static_cast<int>(op)) * 5 + (static_cast<int>(cta) >> 8)) * 3 + red;
+  const int key = ((kind * 8 + static_cast<int>(op)) * 5 + (static_cast<int>(cta) >> 8)) * 3 + red;
   auto it = ctx->occ.find(key);
   if (it != ctx->occ.end()) return it->second;
   int nb = 0;
@@ -212,12 +212,14 @@ uint32_t persistent_grid(irgl_ctx* ctx, uint32_t op, const irgl_tuning& t) {
   return std::max<uint32_t>(grid, 1);
 }
 
+uint32_t op_of(irgl_kernel k) { return k == IRGL_CC_JUMP ? OP_CCJ : static_cast<uint32_t>(k); }
+
 irgl_status check_kernel_graph(irgl_kernel k, const irgl_graph* g) {
   if (k == IRGL_SSSP) {
     if (!g->w) return fail(IRGL_ERR_INVALID_ARG, "SSSP needs edge weights");
     if (g->n > 1 && static_cast<uint64_t>(g->max_w) * (g->n - 1) >= 0xFFFFFFFFull)
       return fail(IRGL_ERR_INVALID_ARG, "max(w) * (n-1) does not fit below INF: uint32 distances could wrap");
-  } else if (k == IRGL_CC) {
+  } else if (k == IRGL_CC || k == IRGL_CC_JUMP) {
     if (!(g->flags & IRGL_SYMMETRIC)) return fail(IRGL_ERR_NOT_SYMMETRIC, "CC needs a graph loaded with IRGL_SYMMETRIC");
   } else if (k != IRGL_BFS) {
     return fail(IRGL_ERR_INVALID_ARG, "unknown kernel %d", static_cast<int>(k));
@@ -249,6 +251,12 @@ KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tu
   p.trace_cap = ctx->trace_cap;
   p.big = (t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{ctx->big_e, ctx->big_off, ctx->big_cap};
   if (ctx->dbg_big_cap && p.big.cap > ctx->dbg_big_cap) p.big.cap = ctx->dbg_big_cap;
+  if ((t.flags & IRGL_TUNE_DIROPT) && (g->in_row_ptr || (g->flags & IRGL_SYMMETRIC))) {
+    p.in_row_ptr = g->in_row_ptr ? g->in_row_ptr : g->row_ptr;
+    p.in_col = g->in_row_ptr ? g->in_col : g->col;
+    p.diropt = ctx->dbg_force_bottom_up ? 2u : 1u;
+    p.m_total = g->m;
+  }
   if (t.delta && ctx->ws_far_stamp && ctx->ws_far_n >= g->n) {
     p.far[0] = ctx->ws_far[0];
     p.far[1] = ctx->ws_far[1];
@@ -388,6 +396,7 @@ irgl_status irgl_debug_set(irgl_ctx* ctx, int key, int64_t value) {
     case 2: ctx->dbg_skip_cta = static_cast<int>(value); return IRGL_OK;
     case 3: ctx->dbg_cap = value > 0 ? static_cast<uint32_t>(value) : 0; return IRGL_OK;
     case 4: ctx->dbg_big_cap = value > 0 ? static_cast<uint32_t>(value) : 0; return IRGL_OK;
+    case 5: ctx->dbg_force_bottom_up = value > 0 ? 1u : 0u; return IRGL_OK;
   }
   return fail(IRGL_ERR_INVALID_ARG, "unknown debug key %d", key);
 }
@@ -433,7 +442,10 @@ irgl_status irgl_csr_load(irgl_ctx* ctx, uint32_t n, uint64_t m, const uint32_t*
                           const int32_t* w, int flags, irgl_graph** out) {
   if (!ctx || !out) return fail(IRGL_ERR_INVALID_ARG, "ctx/out is NULL");
   *out = nullptr;
-  if (flags & ~(IRGL_DEVICE_PTRS | IRGL_SYMMETRIC | IRGL_VALIDATE)) return fail(IRGL_ERR_INVALID_ARG, "unknown flags");
+  if (flags & ~(IRGL_DEVICE_PTRS | IRGL_SYMMETRIC | IRGL_VALIDATE | IRGL_IN_EDGES))
+    return fail(IRGL_ERR_INVALID_ARG, "unknown flags");
+  if ((flags & IRGL_IN_EDGES) && (flags & IRGL_DEVICE_PTRS))
+    return fail(IRGL_ERR_UNSUPPORTED, "IRGL_IN_EDGES needs host pointers");
   if (m >= 0xFFFFFFFFull) return fail(IRGL_ERR_INVALID_ARG, "m must be < 2^32");
   DeviceGuard guard(ctx->device);
   const bool dev = (flags & IRGL_DEVICE_PTRS) != 0;
@@ -500,6 +512,27 @@ irgl_status irgl_csr_load(irgl_ctx* ctx, uint32_t n, uint64_t m, const uint32_t*
       e = cudaMemcpyAsync(g->col, col, sizeof(uint32_t) * m, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess && w && m)
       e = cudaMemcpyAsync(g->w, w, sizeof(int32_t) * m, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && (flags & IRGL_IN_EDGES) && !(flags & IRGL_SYMMETRIC)) {
+      // transpose by counting sort over destinations (rows of the result are in source order)
+      std::vector<uint32_t> irp, icol;
+      try {
+        irp.assign((size_t)n + 1, 0);
+        icol.resize(m);
+      } catch (const std::bad_alloc&) {
+        irgl_graph_destroy(g);
+        return fail(IRGL_ERR_OOM, "in-edge build");
+      }
+      for (uint64_t k = 0; k < m; ++k) ++irp[(size_t)col[k] + 1];
+      for (uint32_t v = 0; v < n; ++v) irp[(size_t)v + 1] += irp[v];
+      std::vector<uint32_t> fillp(irp.begin(), irp.end() - 1);
+      for (uint32_t u = 0; u < n; ++u)
+        for (uint32_t k = row_ptr[u]; k < row_ptr[u + 1]; ++k) icol[fillp[col[k]]++] = u;
+      e = cudaMalloc(&g->in_row_ptr, sizeof(uint32_t) * ((size_t)n + 1));
+      if (e == cudaSuccess) e = cudaMalloc(&g->in_col, sizeof(uint32_t) * std::max<uint64_t>(m, 4));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(g->in_row_ptr, irp.data(), sizeof(uint32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && m) e = cudaMemcpy(g->in_col, icol.data(), sizeof(uint32_t) * m, cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
       irgl_graph_destroy(g);
@@ -519,6 +552,8 @@ irgl_status irgl_graph_destroy(irgl_graph* g) {
     cudaFree(g->col);
     cudaFree(g->w);
   }
+  cudaFree(g->in_row_ptr);
+  cudaFree(g->in_col);
   delete g;
   return IRGL_OK;
 }
@@ -642,7 +677,7 @@ irgl_status irgl_init_state(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_wo
   p.init_count = initial ? initial->tail : nullptr;
   p.init_cap = initial ? initial->cap : 0;
   const uint32_t grid = static_cast<uint32_t>(ctx->sm_count) * 4;
-  cudaError_t e = launch_init_state(static_cast<uint32_t>(k), p, grid, ctx->stream);
+  cudaError_t e = launch_init_state(k == IRGL_CC_JUMP ? OP_CC : static_cast<uint32_t>(k), p, grid, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "init_state launch");
   return IRGL_OK;
 }
@@ -652,6 +687,7 @@ irgl_status irgl_invoke(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workli
   if (!ctx || !g || !in || !out || !state_dev) return fail(IRGL_ERR_INVALID_ARG, "NULL argument");
   if (in == out) return fail(IRGL_ERR_INVALID_ARG, "in and out must be different worklists");
   if (r != IRGL_REDUCE_ANY && r != IRGL_REDUCE_ALL) return fail(IRGL_ERR_INVALID_ARG, "unknown reduction");
+  if (k == IRGL_CC_JUMP) return fail(IRGL_ERR_UNSUPPORTED, "pointer-jumping CC runs only as a persistent Iterate");
   irgl_status s = check_kernel_graph(k, g);
   if (s != IRGL_OK) return s;
   irgl_tuning t;
@@ -697,7 +733,9 @@ irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workl
   DeviceGuard guard(ctx->device);
   s = ensure_workspace(ctx, g->n, k != IRGL_BFS, k == IRGL_SSSP && mode == IRGL_PERSISTENT && t.delta != 0);
   if (s != IRGL_OK) return s;
-  const uint32_t op = static_cast<uint32_t>(k);
+  const uint32_t op = op_of(k);
+  if (k == IRGL_CC_JUMP && mode != IRGL_PERSISTENT)
+    return fail(IRGL_ERR_UNSUPPORTED, "pointer-jumping CC runs only as a persistent Iterate");
   KParams p = make_params(ctx, g, state_dev, t);
   p.init_items = initial ? initial->items : nullptr;
   p.init_count = initial ? initial->tail : nullptr;
@@ -843,7 +881,7 @@ irgl_status irgl_run(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uint32_t
     if (s == IRGL_OK) s = irgl_worklist_push(ctx->run_wl, srcs_host, nsrc);
     if (s != IRGL_OK) return s;
     init = ctx->run_wl;
-  } else if (k != IRGL_CC) {
+  } else if (k != IRGL_CC && k != IRGL_CC_JUMP) {
     return fail(IRGL_ERR_INVALID_ARG, "BFS/SSSP need at least one source");
   }
   uint32_t* dst = state;

@@ -203,6 +203,7 @@ irgl_status irgl_batch_add(irgl_batch* b, irgl_graph* g, irgl_kernel k, const ui
   if (b->prepared) return fail(IRGL_ERR_INVALID_ARG, "batch already prepared");
   if (b->qs.size() >= b->max_q) return fail(IRGL_ERR_INVALID_ARG, "batch is full (%u queries)", b->max_q);
   if (g->ctx != b->ctx) return fail(IRGL_ERR_INVALID_ARG, "graph belongs to another context");
+  if (k == IRGL_CC_JUMP) return fail(IRGL_ERR_UNSUPPORTED, "batches host BFS, SSSP and CC queries");
   irgl_status s = check_kernel_graph(k, g);
   if (s != IRGL_OK) return s;
   if (k != IRGL_CC && nsrc == 0) return fail(IRGL_ERR_INVALID_ARG, "BFS/SSSP need at least one source");

@@ -33,7 +33,7 @@ constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Operator ids (OP_RUNTIME: taken per query from the batch descriptor).
-enum : uint32_t { OP_BFS = 0, OP_SSSP = 1, OP_CC = 2, OP_RUNTIME = 3 };
+enum : uint32_t { OP_BFS = 0, OP_SSSP = 1, OP_CC = 2, OP_RUNTIME = 3, OP_CCJ = 4 };
 enum : int { RED_NONE = 0, RED_ANY = 1, RED_ALL = 2 };
 // Device error codes (first one wins).
 enum : uint32_t {
@@ -83,7 +83,10 @@ struct alignas(128) DevStatus {
   // SSSP near-far: sizes of the two far lists and the smallest distance pushed to each
   uint32_t far_tail[2];
   uint32_t far_min[2];
-  uint32_t pad6[28];
+  uint32_t pad6[4];
+  // direction-optimising BFS: out-edges of the vertices each round pushed (triple-buffered)
+  unsigned long long mf[3];
+  uint32_t pad7[18];
 };
 static_assert(sizeof(DevStatus) == 1152, "status layout");
 
@@ -139,6 +142,11 @@ struct KParams {
   uint32_t far_cap;
   uint32_t* far_stamp;
   uint32_t delta;
+  // direction-optimising BFS (diropt = 0: top-down rounds only)
+  const uint32_t* in_row_ptr;
+  const uint32_t* in_col;
+  uint32_t diropt;
+  unsigned long long m_total;
 };
 
 // Per-launch (one round) arguments.
@@ -208,6 +216,40 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
   return v;
 }
 
+// Adjacency (col, w) loads: read once per round, so (unless IRGL_NO_L2_HINTS) they
+// carry an L2 evict-first policy and skip L1, keeping the randomly accessed
+// state and stamp arrays resident in L2.
+#ifndef IRGL_NO_L2_HINTS
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+template <class T>
+__device__ __forceinline__ T ld_adj(const T* p) {
+  static_assert(sizeof(T) == 4, "scalar adjacency load");
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(l2_evict_first()));
+  return static_cast<T>(v);
+}
+__device__ __forceinline__ uint4 ld_adj4(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(l2_evict_first()));
+  return v;
+}
+__device__ __forceinline__ int4 ld_adj4(const int4* p) {
+  const uint4 v = ld_adj4(reinterpret_cast<const uint4*>(p));
+  return make_int4(static_cast<int>(v.x), static_cast<int>(v.y), static_cast<int>(v.z), static_cast<int>(v.w));
+}
+#else
+template <class T>
+__device__ __forceinline__ T ld_adj(const T* p) { return __ldg(p); }
+__device__ __forceinline__ uint4 ld_adj4(const uint4* p) { return __ldg(p); }
+__device__ __forceinline__ int4 ld_adj4(const int4* p) { return __ldg(p); }
+#endif
+
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
   const uint32_t lane = threadIdx.x & 31;
 #pragma unroll
@@ -231,34 +273,26 @@ __device__ __forceinline__ void set_err(uint32_t* err, uint32_t code) { atomicCA
 
 template <int CTA>
 struct Smem {
-  static constexpr int kStage = 4 * CTA;  // push stage capacity (items)
+  // push stage capacity (items): flushed at tile and phase ends; pushes that
+  // do not fit go straight to the out-worklist (warp-aggregated)
+  static constexpr int kStage = 16 * CTA < 8192 ? 16 * CTA : 8192;
   static constexpr int kWarps = CTA / 32;
   uint32_t stage[kStage];
-  uint32_t s_off[CTA];   // scan bin: exclusive offset of each thread's short list
-  uint32_t s_beg[CTA];   //           first edge of the list
-  uint32_t s_val[CTA];   //           operator value of the popped vertex
-  uint32_t s_q[CTA];     //           query slot (batched)
-  uint32_t warp_sums[kWarps + 1];
   uint32_t stage_n;
   uint32_t gbase;
   uint32_t grab_base;
   uint32_t flag;
-  uint32_t own_tid, own_beg, own_end, own_val, own_q;
-  uint32_t red;
-  uint32_t pub_out;  // out-worklist size published by the grid barrier
-  uint32_t pub_err;  // device error code published by the grid barrier
+  uint32_t own_tid, own_beg, own_end, own_val, own_q;  // CTA bin owner broadcast
+  uint32_t pub_out;                         // out-worklist size published by the grid barrier
+  uint32_t pub_err;                         // device error code published by the grid barrier
   uint32_t round_pushes;                    // out-worklist slots this CTA reserved in the current round
   uint32_t far_min_cta;                     // smallest distance this CTA pushed to the far list
   uint32_t big_appended;                    // this CTA appended to the big list in the current round
   uint32_t pub_flags;                       // kRelBigFlag when the big list is pending
   unsigned long long pub_big;               // published big-list counter
-  unsigned long long big_base;              // this tile's reservation in the big list
-  unsigned long long warp_big[kWarps + 1];
-  static constexpr int kBigWin = 256;       // big-list window held in shared memory
-  uint4 be[kBigWin];                        // entries {beg, end, val, q}
-  unsigned long long bo[kBigWin];           // their first edge in the concatenation
+  unsigned long long mf_cta;                // out-edges of the vertices this CTA pushed this round
   unsigned long long edges;
-  uint8_t pushed[CTA];   // ReduceAndReturn All: item pushed something
+  uint8_t pushed[CTA];                      // ReduceAndReturn All: item pushed something
 };
 
 template <int CTA>
@@ -381,53 +415,33 @@ __device__ __forceinline__ void push4(Smem<CTA>& sm, const Out& out, uint32_t f,
   }
 }
 
-// ----------------------------------------------------------------------------- CTA-wide scan
+// ----------------------------------------------------------------------------- warp helpers
 
-template <int CTA>
-__device__ __forceinline__ uint32_t cta_excl_scan(Smem<CTA>& sm, uint32_t x, uint32_t& total) {
-  constexpr int NW = Smem<CTA>::kWarps;
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t incl = warp_incl_scan(x);
-  if (lane == 31) sm.warp_sums[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    const uint32_t s = lane < static_cast<uint32_t>(NW) ? sm.warp_sums[lane] : 0u;
-    const uint32_t si = warp_incl_scan(s);
-    if (lane < static_cast<uint32_t>(NW)) sm.warp_sums[lane] = si - s;
-    if (lane == static_cast<uint32_t>(NW) - 1) sm.warp_sums[NW] = si;
+// Largest lane j < n whose `key` (held by lane j; non-decreasing over lanes,
+// lane 0's key <= e) is <= e. Five shuffle steps, all lanes together.
+template <class K>
+__device__ __forceinline__ uint32_t warp_find(K key, K e, uint32_t n) {
+  uint32_t lo = 0, hi = n - 1;
+#pragma unroll
+  for (int step = 0; step < 5; ++step) {
+    const uint32_t md = (lo + hi + 1) >> 1;
+    const K km = __shfl_sync(kFull, key, md);
+    if (lo < hi) {
+      if (km <= e) lo = md;
+      else hi = md - 1;
+    }
   }
-  __syncthreads();
-  total = sm.warp_sums[NW];
-  return sm.warp_sums[wid] + incl - x;
+  return lo;
 }
 
-template <int CTA>
-__device__ __forceinline__ unsigned long long cta_excl_scan64(Smem<CTA>& sm, unsigned long long x,
-                                                            unsigned long long& total) {
-  constexpr int NW = Smem<CTA>::kWarps;
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned long long incl = x;
+__device__ __forceinline__ unsigned long long warp_incl_scan64(unsigned long long x) {
+  const uint32_t lane = threadIdx.x & 31;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long t = __shfl_up_sync(kFull, incl, o);
-    if (lane >= static_cast<uint32_t>(o)) incl += t;
+    const unsigned long long t = __shfl_up_sync(kFull, x, o);
+    if (lane >= static_cast<uint32_t>(o)) x += t;
   }
-  if (lane == 31) sm.warp_big[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    const unsigned long long v = lane < static_cast<uint32_t>(NW) ? sm.warp_big[lane] : 0ull;
-    unsigned long long vi = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long t = __shfl_up_sync(kFull, vi, o);
-      if (lane >= static_cast<uint32_t>(o)) vi += t;
-    }
-    if (lane < static_cast<uint32_t>(NW)) sm.warp_big[lane] = vi - v;
-    if (lane == static_cast<uint32_t>(NW) - 1) sm.warp_big[NW] = vi;
-  }
-  __syncthreads();
-  total = sm.warp_big[NW];
-  return sm.warp_big[wid] + incl - x;
+  return x;
 }
 
 // ----------------------------------------------------------------------------- graph views
@@ -551,6 +565,9 @@ struct RoundCtx {
   Out far_out;
   uint32_t* far_stamp;
   uint32_t phase;                 // far-list dedup id of the current phase
+  uint32_t* changes;              // pointer-jumping CC: hooks that lowered a parent (shared memory)
+  unsigned long long* mf;         // direction-optimising BFS: out-degrees of pushed vertices (shared memory)
+  const uint32_t* row_ptr;        //   and the row offsets to take them from
 };
 
 // decide() with the SSSP near-far routing: 0 = no push, 1 = push to this
@@ -561,6 +578,18 @@ template <uint32_t OP>
 __device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state, uint32_t* stamp, uint32_t v,
                                                  uint32_t val, int32_t wt, uint32_t cur, const RoundCtx& rc,
                                                  uint32_t sb, uint32_t& nd_out) {
+  if (OP == OP_CCJ) {
+    // hook: the larger of the two endpoints' parents is pointed at the smaller one
+    if (val == cur) return 0u;
+    const uint32_t lo = min(val, cur), hi = max(val, cur);
+    if (atomicMin(state + hi, lo) > lo) atomicAdd(rc.changes, 1u);
+    return 0u;
+  }
+  if (OP == OP_BFS) {
+    const bool p = decide<OP>(op_rt, state, stamp, v, val, wt, cur, rc.ep);
+    if (p && rc.mf) atomicAdd(rc.mf, static_cast<unsigned long long>(__ldg(rc.row_ptr + v + 1) - __ldg(rc.row_ptr + v)));
+    return p ? 1u : 0u;
+  }
   if (OP != OP_SSSP || rc.limit == kInf) return decide<OP>(op_rt, state, stamp, v, val, wt, cur, rc.ep) ? 1u : 0u;
   const uint32_t nd = val + static_cast<uint32_t>(wt);
   if (nd >= cur) return 0u;
@@ -618,8 +647,8 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
   auto scalar = [&](uint32_t e, uint32_t lim) {
     uint32_t r = 0, v = 0, nd = 0;
     if (e < lim) {
-      v = __ldg(col + e);
-      const int32_t wt = nw ? __ldg(w + e) : 0;
+      v = ld_adj(col + e);
+      const int32_t wt = nw ? ld_adj(w + e) : 0;
       r = decide_route<OP>(op, state, stamp, v, val, wt, __ldcg(state + v), rc, sb, nd);
     }
     push1<CTA>(sm, rc.out, r == 1u, sb + v);
@@ -632,9 +661,9 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
     uint32_t fn = 0, ff = 0, dmin = kInf;
     uint4 c = make_uint4(0, 0, 0, 0);
     if (e < b) {
-      c = __ldg(reinterpret_cast<const uint4*>(col + e));
+      c = ld_adj4(reinterpret_cast<const uint4*>(col + e));
       int4 ww = make_int4(0, 0, 0, 0);
-      if (nw) ww = __ldg(reinterpret_cast<const int4*>(w + e));
+      if (nw) ww = ld_adj4(reinterpret_cast<const int4*>(w + e));
       // all four destination loads in flight before any atomic
       const uint32_t c0 = __ldcg(state + c.x), c1 = __ldcg(state + c.y);
       const uint32_t c2 = __ldcg(state + c.z), c3 = __ldcg(state + c.w);
@@ -668,6 +697,7 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
                                              uint32_t& edges, uint32_t& any_true, uint32_t& any_false) {
   const uint32_t tid = threadIdx.x;
   const uint32_t lane = tid & 31;
+  const uint32_t wbase = tid & ~31u;
   bool valid = idx < rc.in_n;
   uint32_t q = 0, beg = 0, end = 0, val = 0;
   if (valid) {
@@ -690,28 +720,29 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
   edges += deg;
   bool pushed = false;
 
-  // Long lists: with the big list enabled they are appended (one atomic per
-  // tile reserves slots and edge offsets together) and walked by the whole grid
-  // after the round's first barrier; otherwise (or when the list is full) the
-  // CTA bin below walks them.
-  // With the big list on, a frontier smaller than one tile per CTA sends every
-  // list of warp size or more to the grid phase (the few CTAs holding items
-  // would otherwise walk them alone); larger frontiers send lists >= cta_thresh.
+  // Long lists. With the big list on, each warp appends its long lists (one
+  // 64-bit atomic reserves slots and edge offsets together); the whole grid
+  // walks them after the round's first barrier. A frontier smaller than one
+  // tile per CTA sends every list of warp size or more there (the few CTAs
+  // holding items would otherwise walk them alone). Lists that do not fit the
+  // big list fall back to the warp bin. With the big list off (one-launch
+  // rounds), the CTA bin walks lists >= cta_thresh one at a time.
   const uint32_t split = (rc.big.cap != 0 && rc.in_n < gridDim.x * CTA) ? min(rc.tn.warp_thresh, rc.tn.cta_thresh)
                                                                          : rc.tn.cta_thresh;
-  bool big = deg >= split;
-  if (rc.big.cap != 0 && __syncthreads_or(big)) {
-    const unsigned long long mine = big ? ((1ull << 40) | deg) : 0ull;
-    unsigned long long total = 0;
-    const unsigned long long ex = cta_excl_scan64<CTA>(sm, mine, total);
-    if (total != 0) {
-      if (tid == 0) {
-        sm.big_base = atomicAdd(rc.big_ctr, total);
+  bool big = valid && deg >= split;
+  if (rc.big.cap != 0) {
+    if (__any_sync(kFull, big)) {
+      const unsigned long long mine = big ? ((1ull << 40) | deg) : 0ull;
+      const unsigned long long incl = warp_incl_scan64(mine);
+      const unsigned long long total = __shfl_sync(kFull, incl, 31);
+      unsigned long long base = 0;
+      if (lane == 31) {
+        base = atomicAdd(rc.big_ctr, total);
         sm.big_appended = 1;
       }
-      __syncthreads();
+      base = __shfl_sync(kFull, base, 31);
       if (big) {
-        const unsigned long long at = sm.big_base + ex;
+        const unsigned long long at = base + incl - mine;
         const uint32_t slot = static_cast<uint32_t>(at >> 40);
         if (slot < rc.big.cap) {
           rc.big.e[slot] = make_uint4(beg, end, val, q);
@@ -720,26 +751,27 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
         }
       }
     }
-  }
-  // CTA bin: the whole CTA walks one long list at a time.
-  while (__syncthreads_or(big)) {
-    if (big) sm.own_tid = tid;
-    __syncthreads();
-    if (tid == sm.own_tid) {
-      sm.own_beg = beg;
-      sm.own_end = end;
-      sm.own_val = val;
-      sm.own_q = q;
-      big = false;
+  } else {
+    // CTA bin: the whole CTA walks one long list at a time.
+    while (__syncthreads_or(big)) {
+      if (big) sm.own_tid = tid;
+      __syncthreads();
+      if (tid == sm.own_tid) {
+        sm.own_beg = beg;
+        sm.own_end = end;
+        sm.own_val = val;
+        sm.own_q = q;
+        big = false;
+      }
+      __syncthreads();
+      const bool p = group_edges<OP, CTA, CTA>(g, sm, rc, sm.own_q, sm.own_beg, sm.own_end, sm.own_val, tid);
+      if (RED == RED_ALL && p) sm.pushed[sm.own_tid] = 1;
+      pushed |= p;
     }
-    __syncthreads();
-    const bool p = group_edges<OP, CTA, CTA>(g, sm, rc, sm.own_q, sm.own_beg, sm.own_end, sm.own_val, tid);
-    if (RED == RED_ALL && p) sm.pushed[sm.own_tid] = 1;
-    pushed |= p;
   }
 
   // Warp bin: each warp walks its members' medium lists one at a time.
-  bool mid = valid && deg >= rc.tn.warp_thresh && deg < split;
+  bool mid = valid && ((deg >= rc.tn.warp_thresh && deg < split) || big);
   for (;;) {
     const unsigned m = __ballot_sync(kFull, mid);
     if (m == 0) break;
@@ -750,79 +782,71 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
     const uint32_t wq = __shfl_sync(kFull, q, ld);
     if (lane == static_cast<uint32_t>(ld)) mid = false;
     const bool p = group_edges<OP, CTA, 32>(g, sm, rc, wq, wb, we, wv, lane);
-    if (RED == RED_ALL && p) sm.pushed[(tid & ~31u) + ld] = 1;
+    if (RED == RED_ALL && p) sm.pushed[wbase + ld] = 1;
     pushed |= p;
   }
 
-  // Scan bin: short lists of the whole tile, one edge per thread per strip.
+  // Scan bin, per warp: the short lists of the warp's 32 items are dealt out
+  // four edges per lane per strip (strided by 32, so loads coalesce within a
+  // list); each edge finds its list by a shuffle binary search over the
+  // warp's exclusive degree prefix. No CTA barrier is involved.
   const bool small = valid && deg > 0 && deg < rc.tn.warp_thresh && deg < split;
-  uint32_t total = 0;
-  const uint32_t excl = cta_excl_scan<CTA>(sm, small ? deg : 0u, total);
-  if (total > 0) {
-    sm.s_off[tid] = excl;
-    sm.s_beg[tid] = beg;
-    sm.s_val[tid] = val;
-    sm.s_q[tid] = q;
-    __syncthreads();
-    constexpr uint32_t E = 4;  // edges per thread per strip (strided by CTA: coalesced per k)
-    for (uint32_t base = 0; base < total; base += E * CTA) {
-      uint32_t own[E], v[E], cur[E], sb[E], op[E];
-      int32_t wt[E];
+  const uint32_t sdeg = small ? deg : 0u;
+  const uint32_t sincl = warp_incl_scan(sdeg);
+  const uint32_t sexcl = sincl - sdeg;
+  const uint32_t total = __shfl_sync(kFull, sincl, 31);
+  constexpr uint32_t E = 4;
+  for (uint32_t base = 0; base < total; base += E * 32) {
+    uint32_t v[E], cur[E], sb[E], op[E], ov[E], own[E], oqs[E];
+    int32_t wt[E];
 #pragma unroll
-      for (uint32_t k = 0; k < E; ++k) {
-        const uint32_t e = base + k * CTA + tid;
-        own[k] = 0;
-        if (e < total) {
-          uint32_t lo = 0, hi = CTA - 1;
-          while (lo < hi) {
-            const uint32_t md = (lo + hi + 1) >> 1;
-            if (sm.s_off[md] <= e) lo = md;
-            else hi = md - 1;
-          }
-          own[k] = lo;
-        }
-      }
-#pragma unroll
-      for (uint32_t k = 0; k < E; ++k) {
-        const uint32_t e = base + k * CTA + tid;
-        v[k] = 0;
-        wt[k] = 0;
-        sb[k] = 0;
-        op[k] = OP_BFS;
-        if (e < total) {
-          const uint32_t oq = sm.s_q[own[k]];
-          const uint32_t edge = sm.s_beg[own[k]] + (e - sm.s_off[own[k]]);
-          op[k] = g.op(oq);
-          sb[k] = g.sbase(oq);
-          v[k] = __ldg(g.colp(oq) + edge);
-          if (needs_w<OP>(op[k])) wt[k] = __ldg(g.wp(oq) + edge);
-        }
-      }
-#pragma unroll
-      for (uint32_t k = 0; k < E; ++k) cur[k] = (base + k * CTA + tid < total) ? __ldcg(g.state + sb[k] + v[k]) : 0u;
-      uint32_t f = 0, ff = 0, dmin = kInf;
-#pragma unroll
-      for (uint32_t k = 0; k < E; ++k) {
-        uint32_t nd = 0;
-        const uint32_t r = base + k * CTA + tid < total
-                               ? decide_route<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], sm.s_val[own[k]], wt[k],
-                                                  cur[k], rc, sb[k], nd)
-                               : 0u;
-        if (r == 1u) f |= 1u << k;
-        if (r == 2u) {
-          ff |= 1u << k;
-          dmin = min(dmin, nd);
-        }
-        if (r != 0u) {
-          if (RED == RED_ALL) sm.pushed[own[k]] = 1;
-          if (V::kBatched) g.mark(sm.s_q[own[k]], rc.ep);
-        }
-      }
-      push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
-      if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, ff, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3], dmin);
-      pushed |= (f | ff) != 0;
-      if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
+    for (uint32_t k = 0; k < E; ++k) {
+      const uint32_t e = base + k * 32 + lane;
+      own[k] = warp_find<uint32_t>(sexcl, e < total ? e : total - 1, 32);
     }
+#pragma unroll
+    for (uint32_t k = 0; k < E; ++k) {
+      const uint32_t e = base + k * 32 + lane;
+      const uint32_t ob = __shfl_sync(kFull, beg, own[k]);
+      const uint32_t oe = __shfl_sync(kFull, sexcl, own[k]);
+      const uint32_t oq = __shfl_sync(kFull, q, own[k]);
+      oqs[k] = oq;
+      ov[k] = __shfl_sync(kFull, val, own[k]);
+      v[k] = 0;
+      wt[k] = 0;
+      sb[k] = 0;
+      op[k] = OP_BFS;
+      if (e < total) {
+        const uint32_t edge = ob + (e - oe);
+        op[k] = g.op(oq);
+        sb[k] = g.sbase(oq);
+        v[k] = ld_adj(g.colp(oq) + edge);
+        if (needs_w<OP>(op[k])) wt[k] = ld_adj(g.wp(oq) + edge);
+      }
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < E; ++k) cur[k] = (base + k * 32 + lane < total) ? __ldcg(g.state + sb[k] + v[k]) : 0u;
+    uint32_t f = 0, ff = 0, dmin = kInf;
+#pragma unroll
+    for (uint32_t k = 0; k < E; ++k) {
+      uint32_t nd = 0;
+      const uint32_t r = base + k * 32 + lane < total
+                             ? decide_route<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], ov[k], wt[k], cur[k], rc,
+                                                sb[k], nd)
+                             : 0u;
+      if (r == 1u) f |= 1u << k;
+      if (r == 2u) {
+        ff |= 1u << k;
+        dmin = min(dmin, nd);
+      }
+      if (r != 0u) {
+        if (RED == RED_ALL) sm.pushed[wbase + own[k]] = 1;
+        if (V::kBatched) g.mark(oqs[k], rc.ep);
+      }
+    }
+    push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
+    if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, ff, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3], dmin);
+    pushed |= (f | ff) != 0;
   }
 
   if (RED == RED_ANY) any_true |= pushed ? 1u : 0u;
@@ -962,16 +986,16 @@ __device__ __forceinline__ bool grid_barrier(Smem<CTA>& sm, DevStatus* st, uint3
 }
 
 // Largest i in [0, n) with off[i] <= x, for an increasing array with off[0] <= x:
-// the whole CTA samples CTA positions per step (one load each) and narrows the
-// interval by a factor CTA.
-template <int CTA>
-__device__ __forceinline__ uint32_t cta_search_le(const unsigned long long* off, uint32_t n, unsigned long long x) {
+// the warp samples 32 positions per step (one load per lane) and narrows the
+// interval by a factor 32.
+__device__ __forceinline__ uint32_t warp_search_le(const unsigned long long* off, uint32_t n, unsigned long long x) {
+  const uint32_t lane = threadIdx.x & 31;
   uint32_t a = 0, b = n;
   while (b - a > 1) {
-    const uint32_t step = (b - a + CTA - 1) / CTA;
-    const uint32_t p = a + threadIdx.x * step;
+    const uint32_t step = (b - a + 31) / 32;
+    const uint32_t p = a + lane * step;
     const bool pred = p < b && __ldcg(off + p) <= x;
-    const uint32_t c = static_cast<uint32_t>(__syncthreads_count(pred));
+    const uint32_t c = __popc(__ballot_sync(kFull, pred));
     const uint32_t na = a + (c - 1) * step;
     b = min(b, na + step);
     a = na;
@@ -980,89 +1004,79 @@ __device__ __forceinline__ uint32_t cta_search_le(const unsigned long long* off,
 }
 
 // Big phase of a round: the concatenated edges of the big list are split into
-// gridDim.x equal ranges. Each CTA deals its range out to its threads, four
-// edges per thread per strip (strided by CTA so loads coalesce within a list),
-// and finds each edge's list by binary search over a shared-memory window of
-// list offsets; all loads of a strip are issued before its atomics.
+// one equal range per warp of the grid. Each warp holds a window of 32 lists in
+// registers (lane j: list i0 + j), deals its range out four edges per lane per
+// strip (strided by 32, coalesced within a list), and finds each edge's list by
+// a shuffle binary search over the window's offsets; all loads of a strip are
+// issued before its atomics. Only the final stage flush is CTA-wide.
 template <uint32_t OP, int CTA, class V>
 __device__ __forceinline__ void big_phase(const V& g, Smem<CTA>& sm, const RoundCtx& rc, unsigned long long pub) {
-  constexpr uint32_t W = Smem<CTA>::kBigWin;
   constexpr uint32_t E = 4;
+  const uint32_t lane = threadIdx.x & 31;
   const uint32_t n = min(static_cast<uint32_t>(pub >> 40), rc.big.cap);
   const unsigned long long tot = pub & kBigEdgeMask;
-  const unsigned long long lo = tot * blockIdx.x / gridDim.x, hi = tot * (blockIdx.x + 1) / gridDim.x;
-  const uint32_t tid = threadIdx.x;
+  const unsigned long long nw = static_cast<unsigned long long>(gridDim.x) * (CTA / 32);
+  const unsigned long long gw = static_cast<unsigned long long>(blockIdx.x) * (CTA / 32) + (threadIdx.x >> 5);
+  const unsigned long long lo = tot * gw / nw, hi = tot * (gw + 1) / nw;
   if (n != 0 && lo < hi) {
-    uint32_t w0 = cta_search_le<CTA>(rc.big.off, n, lo);
+    uint32_t i0 = warp_search_le(rc.big.off, n, lo);
     unsigned long long pos = lo;
-    while (pos < hi && w0 < n) {
-      __syncthreads();  // previous window no longer read
-      // the window (W entries) may be larger than the CTA: strided load
-      for (uint32_t i = tid; i < W && w0 + i < n; i += CTA) {
-        sm.be[i] = __ldcg(rc.big.e + w0 + i);
-        sm.bo[i] = __ldcg(rc.big.off + w0 + i);
+    while (pos < hi && i0 < n) {
+      const uint32_t lim = min(32u, n - i0);
+      uint4 en = make_uint4(0, 0, 0, 0);
+      unsigned long long off = ~0ull;  // lanes past the window never match
+      if (lane < lim) {
+        en = __ldcg(rc.big.e + i0 + lane);
+        off = __ldcg(rc.big.off + i0 + lane);
       }
-      __syncthreads();
-      const uint32_t lim = min(W, n - w0);
-      const unsigned long long wend_all = sm.bo[lim - 1] + (sm.be[lim - 1].y - sm.be[lim - 1].x);
+      const unsigned long long last_end = off + (en.y - en.x);
+      const unsigned long long wend_all = __shfl_sync(kFull, last_end, lim - 1);
       const unsigned long long wend = wend_all < hi ? wend_all : hi;
-      for (unsigned long long base = pos; base < wend; base += E * CTA) {
-        uint32_t own[E], v[E], cur[E], sb[E], op[E];
+      for (unsigned long long base = pos; base < wend; base += E * 32) {
+        uint32_t v[E], cur[E], sb[E], op[E], ov[E], oqs[E];
         int32_t wt[E];
 #pragma unroll
         for (uint32_t k = 0; k < E; ++k) {
-          const unsigned long long e = base + k * CTA + tid;
-          own[k] = 0;
-          if (e < wend) {
-            uint32_t a = 0, b = lim - 1;
-            while (a < b) {
-              const uint32_t md = (a + b + 1) >> 1;
-              if (sm.bo[md] <= e) a = md;
-              else b = md - 1;
-            }
-            own[k] = a;
-          }
-        }
-#pragma unroll
-        for (uint32_t k = 0; k < E; ++k) {
-          const unsigned long long e = base + k * CTA + tid;
+          const unsigned long long e = base + k * 32 + lane;
+          const uint32_t own = warp_find<unsigned long long>(off, e < wend ? e : wend - 1, lim);
+          const uint32_t ob = __shfl_sync(kFull, en.x, own);
+          const unsigned long long oo = __shfl_sync(kFull, off, own);
+          oqs[k] = __shfl_sync(kFull, en.w, own);
+          ov[k] = __shfl_sync(kFull, en.z, own);
           v[k] = 0;
           wt[k] = 0;
           sb[k] = 0;
           op[k] = OP_BFS;
           if (e < wend) {
-            const uint4 en = sm.be[own[k]];
-            const uint32_t edge = en.x + static_cast<uint32_t>(e - sm.bo[own[k]]);
-            op[k] = g.op(en.w);
-            sb[k] = g.sbase(en.w);
-            v[k] = __ldg(g.colp(en.w) + edge);
-            if (needs_w<OP>(op[k])) wt[k] = __ldg(g.wp(en.w) + edge);
+            const uint32_t edge = ob + static_cast<uint32_t>(e - oo);
+            op[k] = g.op(oqs[k]);
+            sb[k] = g.sbase(oqs[k]);
+            v[k] = ld_adj(g.colp(oqs[k]) + edge);
+            if (needs_w<OP>(op[k])) wt[k] = ld_adj(g.wp(oqs[k]) + edge);
           }
         }
 #pragma unroll
-        for (uint32_t k = 0; k < E; ++k) cur[k] = (base + k * CTA + tid < wend) ? __ldcg(g.state + sb[k] + v[k]) : 0u;
+        for (uint32_t k = 0; k < E; ++k) cur[k] = (base + k * 32 + lane < wend) ? __ldcg(g.state + sb[k] + v[k]) : 0u;
         uint32_t f = 0, ff = 0, dmin = kInf;
 #pragma unroll
         for (uint32_t k = 0; k < E; ++k) {
-          if (base + k * CTA + tid < wend) {
-            const uint4 en = sm.be[own[k]];
+          if (base + k * 32 + lane < wend) {
             uint32_t nd = 0;
             const uint32_t r =
-                decide_route<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], en.z, wt[k], cur[k], rc, sb[k], nd);
+                decide_route<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], ov[k], wt[k], cur[k], rc, sb[k], nd);
             if (r == 1u) f |= 1u << k;
             if (r == 2u) {
               ff |= 1u << k;
               dmin = min(dmin, nd);
             }
-            if (V::kBatched && r != 0u) g.mark(en.w, rc.ep);
+            if (V::kBatched && r != 0u) g.mark(oqs[k], rc.ep);
           }
         }
         push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
         if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, ff, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3], dmin);
-        if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
       }
       pos = wend;
-      w0 += lim;
+      i0 += lim;
     }
   }
   __syncthreads();
@@ -1092,6 +1106,38 @@ __device__ __forceinline__ void init_smem(Smem<CTA>& sm) {
     sm.big_appended = 0;
   }
   __syncthreads();
+}
+
+// Direction-optimising BFS, bottom-up round: every unvisited vertex v scans its
+// in-edges for a parent at the current level L and, at the first one, takes
+// level L + 1 (v is written by this thread only) and joins the out-worklist.
+// Same levels as the top-down round (the fixed point is unique); the work is
+// the in-edges scanned until a parent is found.
+template <int CTA>
+__device__ __forceinline__ void bottom_up_round(const KParams& p, Smem<CTA>& sm, const RoundCtx& rc, uint32_t L,
+                                                uint32_t& edges) {
+  for (uint32_t base = blockIdx.x * CTA; base < p.n; base += gridDim.x * CTA) {
+    const uint32_t v = base + threadIdx.x;
+    bool found = false;
+    if (v < p.n && __ldcg(p.state + v) == kInf) {
+      const uint32_t b = __ldg(p.in_row_ptr + v), e = __ldg(p.in_row_ptr + v + 1);
+      for (uint32_t k = b; k < e; ++k) {
+        ++edges;
+        if (__ldcg(p.state + ld_adj(p.in_col + k)) == L) {
+          found = true;
+          break;
+        }
+      }
+      if (found) {
+        __stcg(p.state + v, L + 1u);
+        atomicAdd(&sm.mf_cta, static_cast<unsigned long long>(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
+      }
+    }
+    push1<CTA>(sm, rc.out, found, v);
+    if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
+  }
+  __syncthreads();
+  flush_stage<CTA>(sm, rc.out);
 }
 
 // SSSP near-far phase change: every item of the finished phase's far list is
@@ -1189,6 +1235,7 @@ __device__ __forceinline__ void persistent_exit(Smem<CTA>& sm, DevStatus* st, bo
     st->big_ctr = 0;
     st->far_tail[0] = st->far_tail[1] = 0;
     st->far_min[0] = st->far_min[1] = 0;
+    st->mf[0] = st->mf[1] = st->mf[2] = 0;
     st->exit_count = 0;
   }
   __threadfence();
@@ -1247,6 +1294,13 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   uint32_t phase = ep0;   // far-list dedup id of the current phase
   uint32_t far_n = 0;
   bool split = false;
+  // direction-optimising BFS (Beamer's rule): go bottom-up when the next
+  // frontier's out-edges exceed the unvisited vertices' out-edges / 15; come
+  // back top-down when the frontier shrinks below n / 18
+  const bool dopt = OP == OP_BFS && p.diropt != 0 && p.in_row_ptr != nullptr;
+  bool bottom_up = dopt && p.diropt == 2;  // test hook: every round bottom-up
+  unsigned long long visited_edges = 0;
+  uint32_t prev_n = init_n;
   uint32_t in_n = init_n;
   for (uint32_t r = 0; ok; ++r) {
     uint32_t* const cur = (r & 1) ? p.items[1] : p.items[0];  // no dynamic index into the param struct
@@ -1264,6 +1318,9 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     rc.limit = limit;
     rc.far_stamp = p.far_stamp;
     rc.phase = phase;
+    rc.changes = nullptr;
+    rc.mf = dopt ? &sm.mf_cta : nullptr;
+    rc.row_ptr = p.row_ptr;
     const uint32_t ftarget = split ? (fb ^ 1u) : fb;  // far list this round pushes to
     rc.far_out = Out{ftarget ? p.far[1] : p.far[0], &st->far_tail[ftarget], p.far_cap, &st->err};
     if (threadIdx.x == 0) {
@@ -1274,11 +1331,20 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
       sm.round_pushes = 0;
       sm.big_appended = 0;
       sm.far_min_cta = kInf;
+      sm.mf_cta = 0;
+      if (dopt && blockIdx.x == 0) st->mf[(r + 2) % 3] = 0;
     }
     if (split) {
       split_far<OP, CTA>(g, sm, rc, fb ? p.far[1] : p.far[0], far_n, lim_old, limit);
+    } else if (dopt && bottom_up) {
+      __syncthreads();
+      bottom_up_round<CTA>(p, sm, rc, r, edges);
     } else {
       round_body<OP, CTA, RED_NONE>(g, sm, rc, edges, dummy_t, dummy_f);
+    }
+    if (dopt && threadIdx.x == 0 && sm.mf_cta) {
+      atomicAdd(&st->mf[r % 3], sm.mf_cta);
+      sm.mf_cta = 0;
     }
     if (nf && threadIdx.x == 0 && sm.far_min_cta != kInf) atomicMax(&st->far_min[ftarget], ~sm.far_min_cta);
     ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns, !split && p.big.cap != 0);
@@ -1286,6 +1352,10 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     if (sm.pub_flags & kRelBigFlag) {
       big_phase<OP, CTA>(g, sm, rc, sm.pub_big);
       if (nf && threadIdx.x == 0 && sm.far_min_cta != kInf) atomicMax(&st->far_min[ftarget], ~sm.far_min_cta);
+      if (dopt && threadIdx.x == 0 && sm.mf_cta) {
+        atomicAdd(&st->mf[r % 3], sm.mf_cta);
+        sm.mf_cta = 0;
+      }
       ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
       if (!ok) break;
     }
@@ -1301,6 +1371,18 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
       }
       fb ^= 1u;
       split = false;
+    }
+    if (dopt && p.diropt == 1 && last_out != 0) {
+      // every CTA takes the same decision from the same published values
+      if (threadIdx.x == 0) sm.pub_big = __ldcg(&st->mf[r % 3]);
+      __syncthreads();
+      const unsigned long long mf = sm.pub_big;
+      __syncthreads();
+      visited_edges += mf;
+      const unsigned long long mu = p.m_total > visited_edges ? p.m_total - visited_edges : 0ull;
+      if (!bottom_up && mf > mu / 15ull && last_out > prev_n) bottom_up = true;
+      else if (bottom_up && last_out < p.n / 18u && last_out < prev_n) bottom_up = false;
+      prev_n = last_out;
     }
     if (last_out == 0) {
       if (!nf) break;
@@ -1332,6 +1414,87 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   persistent_exit<CTA>(sm, st, ok, rounds, last_out, ep0, esum, nullptr, 0);
 }
 
+// Connected components by min-hooking and pointer jumping, in one cooperative
+// launch. parent = state, initially parent[v] = v. Each iteration: (1) hook:
+// for every edge (u, v) with parents a = parent[u], b = parent[v], a != b,
+// atomicMin(parent[max(a,b)], min(a,b)); (2) shortcut: every vertex follows
+// its parent pointers to the root and stores it. Parents only decrease and
+// always name a vertex of the same component, so the first hook phase that
+// lowers nothing leaves every component pointing at one root, its minimum id:
+// the labels of min-label propagation in O(log n) iterations instead of
+// O(diameter) rounds.
+template <int CTA>
+__device__ __forceinline__ void cc_jump_persistent(const KParams& p, Smem<CTA>& sm) {
+  init_smem<CTA>(sm);
+  DevStatus* st = p.st;
+  uint32_t gen = 0;
+  const uint32_t ep0 = __ldcg(&st->epoch);
+  if (p.skip_cta == static_cast<int>(blockIdx.x)) return;  // test hook: never arrives
+  SingleView<OP_CCJ> g{p.row_ptr, p.col, p.w, p.state, p.stamp, p.n};
+  uint32_t edges = 0, dummy_t = 0, dummy_f = 0, rounds = 0, last_changes = 0;
+  fill_state<OP_CC>(p.state, p.n, nullptr, 0, blockIdx.x * CTA + threadIdx.x, gridDim.x * CTA);
+  bool ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
+  trace_round(p.trace, p.trace_cap, 0, p.n, 0);
+  for (uint32_t r = 0; ok; ++r) {
+    RoundCtx rc;
+    rc.in_items = nullptr;  // every vertex
+    rc.in_n = p.n;
+    rc.out = Out{r & 1 ? p.items[0] : p.items[1], &st->tail[(r + 1) % 3], p.cap, &st->err};  // never pushed
+    rc.bfs_val = 0;
+    rc.ep = ep0 + r;
+    rc.grab = &st->grab[r % 3];
+    rc.tn = p.tn;
+    rc.big = p.big;
+    rc.big_ctr = &st->big_ctr;
+    rc.limit = kInf;
+    rc.far_out = Out{nullptr, nullptr, 0, &st->err};
+    rc.far_stamp = nullptr;
+    rc.phase = 0;
+    rc.changes = &sm.round_pushes;  // the barrier publishes the grid's sum
+    rc.mf = nullptr;
+    rc.row_ptr = p.row_ptr;
+    if (threadIdx.x == 0) {
+      if (blockIdx.x == 0) {
+        st->tail[(r + 2) % 3] = 0;
+        st->grab[(r + 2) % 3] = 0;
+      }
+      sm.round_pushes = 0;
+      sm.big_appended = 0;
+    }
+    round_body<OP_CCJ, CTA, RED_NONE>(g, sm, rc, edges, dummy_t, dummy_f);
+    ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns, p.big.cap != 0);
+    if (!ok) break;
+    if (sm.pub_flags & kRelBigFlag) {
+      big_phase<OP_CCJ, CTA>(g, sm, rc, sm.pub_big);
+      ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
+      if (!ok) break;
+    }
+    last_changes = sm.pub_out;
+    // shortcut: every vertex points straight at its root
+    for (uint32_t v = blockIdx.x * CTA + threadIdx.x; v < p.n; v += gridDim.x * CTA) {
+      const uint32_t f0 = __ldcg(p.state + v);
+      uint32_t x = f0;
+      for (;;) {
+        const uint32_t y = __ldcg(p.state + x);
+        if (y == x) break;
+        x = y;
+      }
+      if (x != f0) __stcg(p.state + v, x);
+    }
+    ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
+    if (!ok) break;
+    rounds = r + 1;
+    trace_round(p.trace, p.trace_cap, rounds, p.n, last_changes);
+    if (last_changes == 0 || sm.pub_err != DERR_NONE) break;
+    if (rounds >= p.max_rounds) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) set_err(&st->err, DERR_MAX_ROUNDS);
+      break;
+    }
+  }
+  const unsigned long long esum = cta_sum_u64<CTA>(sm, edges);
+  persistent_exit<CTA>(sm, st, ok, rounds, 0, ep0, esum, nullptr, 0);
+}
+
 // One invocation (Invoke, or one round of a per-launch Iterate).
 template <uint32_t OP, int CTA, int RED>
 __device__ __forceinline__ void invoke_round(const KParams& p, const RoundArgs& a, Smem<CTA>& sm) {
@@ -1353,6 +1516,9 @@ __device__ __forceinline__ void invoke_round(const KParams& p, const RoundArgs& 
   rc.far_out = Out{nullptr, nullptr, 0, &st->err};
   rc.far_stamp = nullptr;
   rc.phase = 0;
+  rc.changes = nullptr;
+  rc.mf = nullptr;
+  rc.row_ptr = p.row_ptr;
   uint32_t edges = 0, any_true = 0, any_false = 0;
   round_body<OP, CTA, RED>(g, sm, rc, edges, any_true, any_false);
   const int t = __syncthreads_or(any_true != 0);
@@ -1443,6 +1609,9 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
     rc.far_out = Out{nullptr, nullptr, 0, &st->err};
     rc.far_stamp = nullptr;
     rc.phase = 0;
+    rc.changes = nullptr;
+    rc.mf = nullptr;
+    rc.row_ptr = nullptr;
     if (threadIdx.x == 0) {
       if (blockIdx.x == 0) {
         st->tail[(r + 2) % 3] = 0;

@@ -40,6 +40,7 @@ struct irgl_ctx {
   int dbg_skip_cta = -1;
   uint32_t dbg_cap = 0;
   uint32_t dbg_big_cap = 0;
+  uint32_t dbg_force_bottom_up = 0;
 };
 
 struct irgl_graph {
@@ -52,6 +53,8 @@ struct irgl_graph {
   bool owns = false;
   int flags = 0;
   int32_t max_w = 0;
+  uint32_t* in_row_ptr = nullptr;  // in-edge CSR (IRGL_IN_EDGES), owned
+  uint32_t* in_col = nullptr;
 };
 
 struct irgl_worklist {
@@ -85,6 +88,7 @@ cudaError_t alloc_big(uint32_t cap, uint4** e, unsigned long long** off);
 int occupancy(irgl_ctx* ctx, int kind, uint32_t op, uint32_t cta, int red);
 uint32_t persistent_grid(irgl_ctx* ctx, uint32_t op, const irgl_tuning& t);
 irgl_status check_kernel_graph(irgl_kernel k, const irgl_graph* g);
+uint32_t op_of(irgl_kernel k);
 KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tuning& t);
 irgl_status tune_descend(const std::function<float(const irgl_tuning&)>& measure, irgl_tuning* best, float* best_ms,
                          bool with_delta = false);

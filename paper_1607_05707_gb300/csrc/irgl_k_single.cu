@@ -1,4 +1,4 @@
-// Persistent cooperative Iterate kernels: BFS / SSSP / CC x CTA size.
+// Persistent cooperative Iterate kernels: BFS / SSSP / CC / pointer-jumping CC x CTA size.
 #include "irgl_launch.h"
 
 namespace irgl {
@@ -6,7 +6,8 @@ namespace irgl {
 template <uint32_t OP, int CTA>
 __global__ void __launch_bounds__(CTA, MinBlocks<CTA>::value) k_iterate(KParams p) {
   __shared__ Smem<CTA> sm;
-  iterate_persistent<OP, CTA>(p, sm);
+  if constexpr (OP == OP_CCJ) cc_jump_persistent<CTA>(p, sm);
+  else iterate_persistent<OP, CTA>(p, sm);
 }
 
 namespace {
@@ -55,6 +56,7 @@ cudaError_t launch_iterate(uint32_t op, uint32_t cta, uint32_t grid, const KPara
     case OP_BFS: return launch_op<OP_BFS>(cta, grid, p, s);
     case OP_SSSP: return launch_op<OP_SSSP>(cta, grid, p, s);
     case OP_CC: return launch_op<OP_CC>(cta, grid, p, s);
+    case OP_CCJ: return launch_op<OP_CCJ>(cta, grid, p, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -64,6 +66,7 @@ cudaError_t occupancy_iterate(uint32_t op, uint32_t cta, int* nb) {
     case OP_BFS: return occ_op<OP_BFS>(cta, nb);
     case OP_SSSP: return occ_op<OP_SSSP>(cta, nb);
     case OP_CC: return occ_op<OP_CC>(cta, nb);
+    case OP_CCJ: return occ_op<OP_CCJ>(cta, nb);
   }
   return cudaErrorInvalidValue;
 }

@@ -78,7 +78,7 @@ extern "C" {
 irgl_status irgl_autotune(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uint32_t* srcs_host, uint32_t nsrc,
                           uint32_t reps, irgl_tuning* best, float* best_ms) {
   if (!ctx || !g || !best || (nsrc && !srcs_host)) return fail(IRGL_ERR_INVALID_ARG, "NULL argument");
-  if (k != IRGL_CC && nsrc == 0) return fail(IRGL_ERR_INVALID_ARG, "BFS/SSSP need at least one source");
+  if (k != IRGL_CC && k != IRGL_CC_JUMP && nsrc == 0) return fail(IRGL_ERR_INVALID_ARG, "BFS/SSSP need at least one source");
   irgl_status s = check_kernel_graph(k, g);
   if (s != IRGL_OK) return s;
   DeviceGuard guard(ctx->device);

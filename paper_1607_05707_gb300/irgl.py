@@ -29,7 +29,7 @@ IRGL_ERR_UNSUPPORTED = -10
 
 IRGL_INF = 0xFFFFFFFF
 
-IRGL_BFS, IRGL_SSSP, IRGL_CC = 0, 1, 2
+IRGL_BFS, IRGL_SSSP, IRGL_CC, IRGL_CC_JUMP = 0, 1, 2, 3
 IRGL_PER_LAUNCH, IRGL_PERSISTENT = 0, 1
 IRGL_REDUCE_ANY, IRGL_REDUCE_ALL = 0, 1
 
@@ -37,9 +37,11 @@ IRGL_HOST_PTRS = 0x0
 IRGL_DEVICE_PTRS = 0x1
 IRGL_SYMMETRIC = 0x2
 IRGL_VALIDATE = 0x4
+IRGL_IN_EDGES = 0x8
 IRGL_TUNE_NO_SPLIT = 0x1
+IRGL_TUNE_DIROPT = 0x2
 
-KERNELS = {"bfs": IRGL_BFS, "sssp": IRGL_SSSP, "cc": IRGL_CC}
+KERNELS = {"bfs": IRGL_BFS, "sssp": IRGL_SSSP, "cc": IRGL_CC, "cc_jump": IRGL_CC_JUMP}
 MODES = {"per_launch": IRGL_PER_LAUNCH, "persistent": IRGL_PERSISTENT}
 
 

@@ -48,13 +48,13 @@ def ctx():
 def run(ctx, kernel, g, dg, srcs, mode="persistent", tuning=None):
     from paper_1607_05707_gb300.api import as_u32
 
-    out, st = ctx.run(kernel, dg, None if kernel == "cc" else srcs, mode=mode, tuning=tuning)
+    out, st = ctx.run(kernel, dg, None if kernel.startswith("cc") else srcs, mode=mode, tuning=tuning)
     return as_u32(out)[: g.n], st
 
 
 def check(ctx, kernel, g, dg, srcs, mode="persistent", tuning=None):
     got, st = run(ctx, kernel, g, dg, srcs, mode, tuning)
-    want = oracle.run(kernel, g, srcs)
+    want = oracle.run("cc" if kernel == "cc_jump" else kernel, g, srcs)
     if not np.array_equal(got, want):
         bad = np.flatnonzero(got != want)
         raise AssertionError(f"{kernel}/{mode}/{tuning}: {bad.size} of {g.n} differ; first {bad[:8]} "
@@ -90,6 +90,8 @@ def test_tiny_random_graphs(ctx):
             check(ctx, "sssp", g, dg, srcs, mode)
             if sym:
                 check(ctx, "cc", g, dg, srcs, mode)
+        if sym:
+            check(ctx, "cc_jump", g, dg, srcs, "persistent")
         dg.close()
 
 
@@ -118,6 +120,7 @@ def test_special_shapes(ctx):
         dg = ctx.load(g, symmetric=True)
         for mode in MODES:
             check(ctx, "cc", g, dg, None, mode)
+        check(ctx, "cc_jump", g, dg, None, "persistent")
         dg.close()
 
 
@@ -155,6 +158,32 @@ def test_mesh_bfs_cc(ctx, tuning):
         check(ctx, "bfs", g, dg, np.array([0], np.uint32), mode, tuning)
         check(ctx, "cc", g, dg, None, mode, tuning)
     check(ctx, "sssp", g, dg, np.array([1234], np.uint32), "persistent", tuning)
+    check(ctx, "cc_jump", g, dg, None, "persistent", tuning)
+    dg.close()
+
+
+@pytest.mark.parametrize("tuning", SCHEDULES[:5])
+def test_cc_jump_many_components(ctx, tuning):
+    # heavily cut mesh (many components) and a symmetric R-MAT graph (hubs, isolated vertices)
+    g = inputs.mesh(200, 170, seed=13, del_frac=0.45, extra_frac=0.01, radius=8)
+    dg = ctx.load(g)
+    st = check(ctx, "cc_jump", g, dg, None, "persistent", tuning)
+    assert st["rounds"] < 64
+    dg.close()
+    r = inputs.rmat(14, 8, seed=14, weights=False)
+    u = np.repeat(np.arange(r.n), np.diff(r.row_ptr.astype(np.int64)))
+    sym = inputs.csr_from_edges(r.n, np.concatenate([u, r.col]), np.concatenate([r.col, u]), symmetric=True)
+    ds = ctx.load(sym)
+    check(ctx, "cc_jump", sym, ds, None, "persistent", tuning)
+    check(ctx, "cc", sym, ds, None, "persistent", tuning)
+    ds.close()
+
+
+def test_cc_jump_mesh4096_full(ctx):
+    g, _ = inputs.workload_mesh(4096)
+    dg = ctx.load(g, validate=False)
+    st = check(ctx, "cc_jump", g, dg, None, "persistent")
+    assert st["rounds"] < 64
     dg.close()
 
 
@@ -274,6 +303,13 @@ def test_errors_and_recovery(ctx):
             ctx.run("bfs", dg, s, mode=mode, max_rounds=2)
         assert ei.value.status == C.IRGL_ERR_MAX_ROUNDS
     check(ctx, "sssp", g, dg, s, "per_launch")
+    # pointer-jumping CC is a persistent-only Iterate
+    gs = inputs.grid(8)
+    dgs = ctx.load(gs)
+    with pytest.raises(C.IrglError) as ei:
+        ctx.run("cc_jump", dgs, None, mode="per_launch")
+    assert ei.value.status == C.IRGL_ERR_UNSUPPORTED
+    dgs.close()
     # CC on a graph not loaded as symmetric
     with pytest.raises(C.IrglError) as ei:
         ctx.run("cc", dg, None)
@@ -304,7 +340,51 @@ def test_big_list_overflow_falls_back(ctx):
     dg.close()
 
 
+DIROPT = [dict(flags=2), dict(flags=2, cta_size=256, warp_thresh=8, cta_thresh=64), dict(flags=3, cta_size=512)]
+
+
+@pytest.mark.parametrize("tuning", DIROPT)
+def test_direction_optimising_bfs(ctx, tuning):
+    g = inputs.rmat(16, 16, seed=51, weights=True)
+    dg = ctx.load(g, in_edges=True)
+    for s in inputs.sources(g, 3, seed=52):
+        check(ctx, "bfs", g, dg, np.array([s], np.uint32), "persistent", tuning)
+    check(ctx, "bfs", g, dg, inputs.sources(g, 5, seed=53), "persistent", tuning)
+    dg.close()
+    m = inputs.mesh(300, 300, seed=54, del_frac=0.01, extra_frac=0.001)  # symmetric: in-edges = out-edges
+    dm = ctx.load(m)
+    check(ctx, "bfs", m, dm, np.array([0], np.uint32), "persistent", tuning)
+    dm.close()
+
+
+def test_bottom_up_every_round(ctx):
+    # test hook: every round bottom-up, on tiny random, special and directed graphs
+    rng = np.random.default_rng(57)
+    ctx.debug_set(5, 1)
+    try:
+        for trial in range(16):
+            n = int(rng.integers(1, 150))
+            g = tiny_graph(rng, n, float(rng.choice([0.02, 0.08])), bool(trial % 2))
+            dg = ctx.load(g, in_edges=True)
+            check(ctx, "bfs", g, dg, rng.integers(0, n, size=2).astype(np.uint32), "persistent", dict(flags=2))
+            dg.close()
+        g = inputs.rmat(13, 8, seed=58, weights=False)
+        dg = ctx.load(g, in_edges=True)
+        check(ctx, "bfs", g, dg, inputs.sources(g, 1, seed=59), "persistent", dict(flags=2))
+        dg.close()
+    finally:
+        ctx.debug_set(5, 0)
+
+
 # ----------------------------------------------------------------------------- configuration sizes
+
+def test_rmat20_bfs_direction_optimising_full(ctx):
+    g, srcs = inputs.workload_rmat20(nsrc=3)
+    dg = ctx.load(g, validate=False, in_edges=True)
+    for s in srcs:
+        check(ctx, "bfs", g, dg, np.array([s], np.uint32), "persistent", dict(flags=2))
+    dg.close()
+
 
 @pytest.mark.parametrize("mode", MODES)
 def test_rmat20_bfs_sssp_full(ctx, mode):
