@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--tuning", type=str, default="", help="JSON irgl_tuning overrides")
     ap.add_argument("--trace", action="store_true", help="print a per-round trace of one query per kernel to stderr")
+    ap.add_argument("--diropt", action="store_true",
+                    help="BFS direction-optimising (bottom-up rounds on large frontiers; loads the in-edge CSR)")
     return ap.parse_args()
 
 
@@ -309,8 +311,14 @@ def run_gpu(args, world, rank, local):
 
     stream = torch.cuda.Stream(device=dev)
     ctx = Context(local, stream)
-    dg = ctx.load(g, validate=False)
+    dg = ctx.load(g, validate=False, in_edges=args.diropt)
     out = {k: ctx.state(g.n) for k in kernels}
+    ktune = {}
+    for k in kernels:
+        t = dict(tuning or {})
+        if args.diropt and k == "bfs":
+            t["flags"] = int(t.get("flags", 0)) | 2
+        ktune[k] = t or None
     wls = []
     for s in srcs:
         wl = ctx.worklist(4)
@@ -328,7 +336,7 @@ def run_gpu(args, world, rank, local):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.iterate_async(k, dg, wls[j], out[k], tuning=tuning)
+            ctx.iterate_async(k, dg, wls[j], out[k], tuning=ktune[k])
             e1.record(stream)
             ev[k] = (e0, e1)
         ctx.sync()
@@ -342,13 +350,13 @@ def run_gpu(args, world, rank, local):
     counts, scanned = {}, {k: 0 for k in kernels}
     for j in sorted(set(used)):
         for k in kernels:
-            ctx.iterate_async(k, dg, wls[j], out[k], tuning=tuning)
+            ctx.iterate_async(k, dg, wls[j], out[k], tuning=ktune[k])
             scanned[k] += ctx.sync()["edges_scanned"]
             counts[(j, k)] = reached_stats(g, as_u32(out[k])[: g.n])
     if args.trace and rank == 0:
         C.irgl_trace_enable(ctx.handle, 1 << 16)
         for k in kernels:
-            ctx.iterate_async(k, dg, wls[used[0]], out[k], tuning=tuning)
+            ctx.iterate_async(k, dg, wls[used[0]], out[k], tuning=ktune[k])
             st = ctx.sync()
             t, a, o = C.irgl_trace_read(ctx.handle)
             print(f"# trace {k} source {srcs[used[0]]}: rounds={st['rounds']} total_us={(int(t[-1]) - int(t[0])) / 1e3:.1f}",
@@ -409,7 +417,7 @@ def run_gpu(args, world, rank, local):
         s = np.array([srcs[(args.warmup + i) % len(srcs)]], np.uint32)
         for k in kernels:
             t0 = time.perf_counter()
-            ctx.run_host(k, dg, s, out=host_out)
+            ctx.run_host(k, dg, s, out=host_out, tuning=ktune[k])
             e2e_t += time.perf_counter() - t0
             e2e_edges += reached_stats(g, host_out)[1]
     e2e_max = max_over_ranks(e2e_t, world, dev)
@@ -425,7 +433,8 @@ def run_gpu(args, world, rank, local):
             "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * t_max / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": dict(workload=name, **meta, mode="persistent (iteration-outlined cooperative launch)",
+            "config": dict(workload=name, **meta, mode="persistent (iteration-outlined cooperative launch)"
+                           + (", BFS direction-optimising" if args.diropt else ""),
                            parallelism=f"replicas x{world} (queries sharded, no collective)",
                            l2="flushed between steps (512 MB write, outside the events)",
                            tuning=tuning or ctx.default_tuning),
