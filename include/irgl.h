@@ -97,6 +97,14 @@ typedef struct {
 #define IRGL_TUNE_DIROPT 0x2u /* persistent BFS: rounds with a large frontier run bottom-up (every
                                  unvisited vertex looks for a parent among its in-edges); needs a
                                  symmetric graph or one loaded with IRGL_IN_EDGES, else ignored */
+#define IRGL_TUNE_BITMAP 0x4u /* persistent BFS: a 1-bit-per-vertex copy of "level != INF", read
+                                 through L1, filters edges to visited vertices before the level is
+                                 read from L2 (off by default: slower on R-MAT scale 20, where the
+                                 bit updates cost more than the L2 reads they save) */
+#define IRGL_TUNE_NO_PACKED 0x8u /* persistent SSSP without near-far: keep distances and the
+                                    dedup stamps in two arrays (by default one 64-bit word per
+                                    vertex holds both, lowered by one atomicMin, and the distances
+                                    are copied to the output at the end) */
 
 /* Per-call counters. */
 typedef struct {
@@ -118,7 +126,9 @@ const char* irgl_status_string(irgl_status s);
  * A context binds a device and a CUDA stream (cudaStream_t passed as void*;
  * NULL = the legacy default stream). It owns the device status block and the
  * scratch worklists/stamps that Iterate uses. One context must not be used
- * from two host threads at once. */
+ * from two host threads at once. Graphs, worklists, batches and servers made
+ * on a context keep a pointer to it: destroy them before the context (their
+ * destroy functions read it). */
 irgl_status irgl_ctx_create(int device, void* cuda_stream, irgl_ctx** out);
 irgl_status irgl_ctx_destroy(irgl_ctx* ctx);
 irgl_status irgl_ctx_set_stream(irgl_ctx* ctx, void* cuda_stream);

@@ -5,6 +5,8 @@ libirgl.so's kernels through the same-name functions of :mod:`.irgl`.
 """
 from __future__ import annotations
 
+import weakref
+
 import numpy as np
 import torch
 
@@ -32,6 +34,7 @@ class Graph:
         w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.int32)
         self.weighted = w is not None
         self.handle = C.irgl_csr_load(ctx.handle, g.n, g.m, _np_ptr(rp), _np_ptr(col), _np_ptr(w), flags)
+        ctx._adopt(self)
 
     def close(self) -> None:
         if self.handle:
@@ -50,6 +53,7 @@ class Worklist:
         self.ctx = ctx
         self.capacity = capacity
         self.handle = C.irgl_worklist_create(ctx.handle, capacity)
+        ctx._adopt(self)
 
     def push(self, items) -> None:
         a = np.ascontiguousarray(np.atleast_1d(items), dtype=np.uint32)
@@ -89,6 +93,11 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         self.handle = C.irgl_ctx_create(device, self.stream.cuda_stream)
         self.sm_count, self.default_tuning = C.irgl_ctx_info(self.handle)
+        # objects made on this context: the library frees them before the context
+        self._children: weakref.WeakSet = weakref.WeakSet()
+
+    def _adopt(self, obj) -> None:
+        self._children.add(obj)
 
     def load(self, g: CSR, symmetric: bool | None = None, validate: bool = True, in_edges: bool = False) -> Graph:
         return Graph(self, g, symmetric, validate, in_edges)
@@ -146,6 +155,12 @@ class Context:
 
     def close(self) -> None:
         if self.handle:
+            # servers and batches hold graphs; graphs and worklists hold the context
+            live = list(self._children)
+            for kind in (Server, Batch, Worklist, Graph):
+                for obj in live:
+                    if isinstance(obj, kind):
+                        obj.close()
             C.irgl_ctx_destroy(self.handle)
             self.handle = 0
 
@@ -161,6 +176,7 @@ class Batch:
     def __init__(self, ctx: Context, max_queries: int = 1024):
         self.ctx = ctx
         self.handle = C.irgl_batch_create(ctx.handle, max_queries)
+        ctx._adopt(self)
         self.sizes: list[int] = []
 
     def add(self, kernel: str, g: Graph, srcs=None) -> int:
@@ -207,6 +223,7 @@ class Server:
                  count_edges: bool = True, tuning=None):
         self.ctx = ctx
         self.handle = C.irgl_server_create(ctx.handle, arena_bytes, max_slots, epoch_rounds, int(count_edges), tuning)
+        ctx._adopt(self)
 
     def submit(self, kernel: str, g: Graph, src: int, out: np.ndarray | None = None) -> int:
         return C.irgl_server_submit(self.handle, g.handle, C.KERNELS[kernel], int(src), _np_ptr(out))

@@ -136,7 +136,7 @@ cudaError_t alloc_big(uint32_t cap, uint4** e, unsigned long long** off) {
   return r;
 }
 
-irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool need_far) {
+irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool need_far, bool need_vis, bool need_ds) {
   if (need_far && n > ctx->ws_far_n) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->ws_far[0]);
@@ -176,6 +176,25 @@ irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool ne
     if (e == cudaSuccess) e = cudaMalloc(&ctx->ws_items[1], sizeof(uint32_t) * (size_t)cap);
     if (e != cudaSuccess) return cuda_fail(e, "worklist allocation");
     ctx->ws_cap = cap;
+  }
+  if (need_vis && (n + 31u) / 32u > ctx->ws_vis_words) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws_vis);
+    ctx->ws_vis = nullptr;
+    ctx->ws_vis_words = 0;
+    const uint32_t words = (n + 31u) / 32u;
+    cudaError_t e = cudaMalloc(&ctx->ws_vis, sizeof(uint32_t) * (size_t)words);
+    if (e != cudaSuccess) return cuda_fail(e, "visited bitmap allocation");
+    ctx->ws_vis_words = words;
+  }
+  if (need_ds && n > ctx->ws_ds_n) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws_ds);
+    ctx->ws_ds = nullptr;
+    ctx->ws_ds_n = 0;
+    cudaError_t e = cudaMalloc(&ctx->ws_ds, sizeof(unsigned long long) * (size_t)n);
+    if (e != cudaSuccess) return cuda_fail(e, "packed distance allocation");
+    ctx->ws_ds_n = n;
   }
   if (need_stamp && n > ctx->ws_stamp_n) {
     cudaStreamSynchronize(ctx->stream);
@@ -324,6 +343,8 @@ irgl_status irgl_ctx_destroy(irgl_ctx* ctx) {
   cudaFree(ctx->ws_items[0]);
   cudaFree(ctx->ws_items[1]);
   cudaFree(ctx->ws_stamp);
+  cudaFree(ctx->ws_vis);
+  cudaFree(ctx->ws_ds);
   cudaFree(ctx->ws_far[0]);
   cudaFree(ctx->ws_far[1]);
   cudaFree(ctx->ws_far_stamp);
@@ -731,7 +752,10 @@ irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workl
   s = resolve_tuning(tin, &t);
   if (s != IRGL_OK) return s;
   DeviceGuard guard(ctx->device);
-  s = ensure_workspace(ctx, g->n, k != IRGL_BFS, k == IRGL_SSSP && mode == IRGL_PERSISTENT && t.delta != 0);
+  const bool vis = k == IRGL_BFS && mode == IRGL_PERSISTENT && (t.flags & IRGL_TUNE_BITMAP);
+  const bool packed = k == IRGL_SSSP && mode == IRGL_PERSISTENT && t.delta == 0 && !(t.flags & IRGL_TUNE_NO_PACKED);
+  s = ensure_workspace(ctx, g->n, k != IRGL_BFS, k == IRGL_SSSP && mode == IRGL_PERSISTENT && t.delta != 0, vis,
+                       packed);
   if (s != IRGL_OK) return s;
   const uint32_t op = op_of(k);
   if (k == IRGL_CC_JUMP && mode != IRGL_PERSISTENT)
@@ -741,6 +765,8 @@ irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workl
   p.init_count = initial ? initial->tail : nullptr;
   p.init_cap = initial ? initial->cap : 0;
   p.max_rounds = max_rounds ? max_rounds : 0xFFFFFFFFu;
+  if (vis) p.vis = ctx->ws_vis;
+  if (packed) p.ds = ctx->ws_ds;
   irgl_stats local;
   std::memset(&local, 0, sizeof(local));
   local.cta_size = t.cta_size;

@@ -147,6 +147,13 @@ struct KParams {
   const uint32_t* in_col;
   uint32_t diropt;
   unsigned long long m_total;
+  // BFS visited bitmap (bit v set => level[v] != INF), ceil(n / 32) words,
+  // cleared in the prologue; nullptr = off
+  uint32_t* vis;
+  // SSSP: per vertex (dist << 32) | id of the round that last lowered it, n
+  // words, filled in the prologue and copied out to `state` at the end;
+  // nullptr = dist in `state` and dedup stamps in `stamp`
+  unsigned long long* ds;
 };
 
 // Per-launch (one round) arguments.
@@ -568,7 +575,23 @@ struct RoundCtx {
   uint32_t* changes;              // pointer-jumping CC: hooks that lowered a parent (shared memory)
   unsigned long long* mf;         // direction-optimising BFS: out-degrees of pushed vertices (shared memory)
   const uint32_t* row_ptr;        //   and the row offsets to take them from
+  uint32_t* vis;                  // BFS visited bitmap, or nullptr
+  unsigned long long* ds;         // SSSP packed (dist, round id) words, or nullptr
+  uint32_t dsr;                   //   and this round's id in them (1, 2, ...)
 };
+
+// The destination's current value as the operator reads it. BFS with the
+// visited bitmap: the bit is read through L1 (a 128 KB bitmap of 2^20 vertices
+// stays there, where the 4 MB level array would be read from L2 per edge). A
+// bit is set only after the level is written, so a set bit is always right; a
+// stale clear bit (set later in this round, or cached before) falls through
+// to the L2 read of the level, which decides.
+template <uint32_t OP>
+__device__ __forceinline__ uint32_t load_cur(const RoundCtx& rc, const uint32_t* state, uint32_t v) {
+  if (OP == OP_BFS && rc.vis != nullptr && ((rc.vis[v >> 5] >> (v & 31u)) & 1u)) return 0u;
+  if (OP == OP_SSSP && rc.ds != nullptr) return static_cast<uint32_t>(__ldcg(rc.ds + v) >> 32);
+  return __ldcg(state + v);
+}
 
 // decide() with the SSSP near-far routing: 0 = no push, 1 = push to this
 // round's out-worklist, 2 = push to the far list. Near pushes dedup on the
@@ -587,8 +610,17 @@ __device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state
   }
   if (OP == OP_BFS) {
     const bool p = decide<OP>(op_rt, state, stamp, v, val, wt, cur, rc.ep);
+    if (p && rc.vis) atomicOr(rc.vis + (v >> 5), 1u << (v & 31u));
     if (p && rc.mf) atomicAdd(rc.mf, static_cast<unsigned long long>(__ldg(rc.row_ptr + v + 1) - __ldg(rc.row_ptr + v)));
     return p ? 1u : 0u;
+  }
+  if (OP == OP_SSSP && rc.ds != nullptr) {
+    // one 64-bit atomicMin lowers the distance and stamps the round: v is
+    // pushed by the thread that lowers it first in this round
+    const uint32_t nd = val + static_cast<uint32_t>(wt);
+    if (nd >= cur) return 0u;
+    const unsigned long long old = atomicMin(rc.ds + v, (static_cast<unsigned long long>(nd) << 32) | rc.dsr);
+    return (nd < static_cast<uint32_t>(old >> 32) && static_cast<uint32_t>(old) != rc.dsr) ? 1u : 0u;
   }
   if (OP != OP_SSSP || rc.limit == kInf) return decide<OP>(op_rt, state, stamp, v, val, wt, cur, rc.ep) ? 1u : 0u;
   const uint32_t nd = val + static_cast<uint32_t>(wt);
@@ -598,6 +630,72 @@ __device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state
   if (nd < rc.limit) return atomicExch(stamp + v, rc.ep) != rc.ep ? 1u : 0u;
   nd_out = nd;
   return atomicExch(rc.far_stamp + sb + v, rc.phase) != rc.phase ? 2u : 0u;
+}
+
+// The operator on N edges of one lane at once. Every atomic whose result
+// decides a push is issued before any of those results is read, so the N L2
+// round trips overlap instead of following one another. Same outcome as
+// decide_route edge by edge (which near-far SSSP and pointer-jumping CC keep
+// using). `state`/`stamp` are array bases, edge k's vertex is sb[k] + v[k].
+template <uint32_t OP, int N>
+__device__ __forceinline__ void decide_n(const RoundCtx& rc, uint32_t* state, uint32_t* stamp,
+                                         const uint32_t (&op)[N], const uint32_t (&sb)[N], const uint32_t (&v)[N],
+                                         const uint32_t (&val)[N], const int32_t (&wt)[N], const uint32_t (&cur)[N],
+                                         uint32_t valid, uint32_t (&r)[N], uint32_t (&nd)[N]) {
+  if (OP == OP_CCJ || (OP == OP_SSSP && rc.limit != kInf)) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      nd[k] = 0;
+      r[k] = ((valid >> k) & 1u) ? decide_route<OP>(op[k], state + sb[k], stamp + sb[k], v[k], val[k], wt[k], cur[k],
+                                                      rc, sb[k], nd[k])
+                                 : 0u;
+    }
+    return;
+  }
+  bool t[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const uint32_t o = OP == OP_RUNTIME ? op[k] : OP;
+    nd[k] = o == OP_SSSP ? val[k] + static_cast<uint32_t>(wt[k]) : val[k];
+    t[k] = ((valid >> k) & 1u) != 0 && (o == OP_BFS ? cur[k] == kInf : nd[k] < cur[k]);
+  }
+  if (OP == OP_SSSP && rc.ds != nullptr) {
+    unsigned long long old[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      old[k] = t[k] ? atomicMin(rc.ds + v[k], (static_cast<unsigned long long>(nd[k]) << 32) | rc.dsr) : 0ull;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      r[k] = (t[k] && nd[k] < static_cast<uint32_t>(old[k] >> 32) && static_cast<uint32_t>(old[k]) != rc.dsr) ? 1u : 0u;
+    return;
+  }
+  uint32_t old[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const uint32_t o = OP == OP_RUNTIME ? op[k] : OP;
+    uint32_t* const s = state + sb[k] + v[k];
+    old[k] = 0u;
+    if (t[k]) old[k] = o == OP_BFS ? atomicCAS(s, kInf, nd[k]) : atomicMin(s, nd[k]);
+  }
+  bool imp[N];
+  uint32_t ex[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const uint32_t o = OP == OP_RUNTIME ? op[k] : OP;
+    imp[k] = t[k] && (o == OP_BFS ? old[k] == kInf : nd[k] < old[k]);
+    ex[k] = ~rc.ep;
+    if (imp[k] && o != OP_BFS) ex[k] = atomicExch(stamp + sb[k] + v[k], rc.ep);
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const uint32_t o = OP == OP_RUNTIME ? op[k] : OP;
+    r[k] = (imp[k] && (o == OP_BFS || ex[k] != rc.ep)) ? 1u : 0u;
+    if (OP == OP_BFS && r[k] != 0u) {
+      if (rc.vis) atomicOr(rc.vis + (v[k] >> 5), 1u << (v[k] & 31u));
+      if (rc.mf)
+        atomicAdd(rc.mf, static_cast<unsigned long long>(__ldg(rc.row_ptr + v[k] + 1) - __ldg(rc.row_ptr + v[k])));
+    }
+  }
 }
 
 // Far-list pushes: warp-aggregated straight to global memory (rare next to
@@ -649,7 +747,7 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
     if (e < lim) {
       v = ld_adj(col + e);
       const int32_t wt = nw ? ld_adj(w + e) : 0;
-      r = decide_route<OP>(op, state, stamp, v, val, wt, __ldcg(state + v), rc, sb, nd);
+      r = decide_route<OP>(op, state, stamp, v, val, wt, load_cur<OP>(rc, state, v), rc, sb, nd);
     }
     push1<CTA>(sm, rc.out, r == 1u, sb + v);
     if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, r == 2u ? 1u : 0u, sb + v, 0u, 0u, 0u, nd);
@@ -664,18 +762,23 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
       c = ld_adj4(reinterpret_cast<const uint4*>(col + e));
       int4 ww = make_int4(0, 0, 0, 0);
       if (nw) ww = ld_adj4(reinterpret_cast<const int4*>(w + e));
-      // all four destination loads in flight before any atomic
-      const uint32_t c0 = __ldcg(state + c.x), c1 = __ldcg(state + c.y);
-      const uint32_t c2 = __ldcg(state + c.z), c3 = __ldcg(state + c.w);
-      uint32_t nd0 = 0, nd1 = 0, nd2 = 0, nd3 = 0;
-      const uint32_t r0 = decide_route<OP>(op, state, stamp, c.x, val, ww.x, c0, rc, sb, nd0);
-      const uint32_t r1 = decide_route<OP>(op, state, stamp, c.y, val, ww.y, c1, rc, sb, nd1);
-      const uint32_t r2 = decide_route<OP>(op, state, stamp, c.z, val, ww.z, c2, rc, sb, nd2);
-      const uint32_t r3 = decide_route<OP>(op, state, stamp, c.w, val, ww.w, c3, rc, sb, nd3);
-      fn = (r0 == 1u ? 1u : 0u) | (r1 == 1u ? 2u : 0u) | (r2 == 1u ? 4u : 0u) | (r3 == 1u ? 8u : 0u);
-      if (OP == OP_SSSP) {
-        ff = (r0 == 2u ? 1u : 0u) | (r1 == 2u ? 2u : 0u) | (r2 == 2u ? 4u : 0u) | (r3 == 2u ? 8u : 0u);
-        dmin = min(min(r0 == 2u ? nd0 : kInf, r1 == 2u ? nd1 : kInf), min(r2 == 2u ? nd2 : kInf, r3 == 2u ? nd3 : kInf));
+      // all four destination loads in flight before any atomic, then all four atomics
+      const uint32_t vv[4] = {c.x, c.y, c.z, c.w};
+      const int32_t wv[4] = {ww.x, ww.y, ww.z, ww.w};
+      const uint32_t ops[4] = {op, op, op, op};
+      const uint32_t zero[4] = {0u, 0u, 0u, 0u};
+      const uint32_t vals[4] = {val, val, val, val};
+      uint32_t cc[4], rr[4], ndv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cc[k] = load_cur<OP>(rc, state, vv[k]);
+      decide_n<OP, 4>(rc, state, stamp, ops, zero, vv, vals, wv, cc, 0xFu, rr, ndv);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (rr[k] == 1u) fn |= 1u << k;
+        if (OP == OP_SSSP && rr[k] == 2u) {
+          ff |= 1u << k;
+          dmin = min(dmin, ndv[k]);
+        }
       }
     }
     push4<CTA>(sm, rc.out, fn, sb + c.x, sb + c.y, sb + c.z, sb + c.w);
@@ -713,6 +816,7 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
       end = __ldg(rp + u + 1);
       const uint32_t op = g.op(q);
       if (op == OP_BFS) val = V::kBatched ? __ldcg(g.state + item) + 1u : rc.bfs_val;
+      else if (OP == OP_SSSP && rc.ds != nullptr) val = static_cast<uint32_t>(__ldcg(rc.ds + item) >> 32);
       else val = __ldcg(g.state + item);
     }
   }
@@ -825,19 +929,19 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
       }
     }
 #pragma unroll
-    for (uint32_t k = 0; k < E; ++k) cur[k] = (base + k * 32 + lane < total) ? __ldcg(g.state + sb[k] + v[k]) : 0u;
-    uint32_t f = 0, ff = 0, dmin = kInf;
+    for (uint32_t k = 0; k < E; ++k)
+      cur[k] = (base + k * 32 + lane < total) ? load_cur<OP>(rc, g.state + sb[k], v[k]) : 0u;
+    uint32_t f = 0, ff = 0, dmin = kInf, vmask = 0, rr[E], ndv[E];
+#pragma unroll
+    for (uint32_t k = 0; k < E; ++k) vmask |= (base + k * 32 + lane < total ? 1u : 0u) << k;
+    decide_n<OP, 4>(rc, g.state, g.stamp, op, sb, v, ov, wt, cur, vmask, rr, ndv);
 #pragma unroll
     for (uint32_t k = 0; k < E; ++k) {
-      uint32_t nd = 0;
-      const uint32_t r = base + k * 32 + lane < total
-                             ? decide_route<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], ov[k], wt[k], cur[k], rc,
-                                                sb[k], nd)
-                             : 0u;
+      const uint32_t r = rr[k];
       if (r == 1u) f |= 1u << k;
       if (r == 2u) {
         ff |= 1u << k;
-        dmin = min(dmin, nd);
+        dmin = min(dmin, ndv[k]);
       }
       if (r != 0u) {
         if (RED == RED_ALL) sm.pushed[wbase + own[k]] = 1;
@@ -1056,21 +1160,21 @@ __device__ __forceinline__ void big_phase(const V& g, Smem<CTA>& sm, const Round
           }
         }
 #pragma unroll
-        for (uint32_t k = 0; k < E; ++k) cur[k] = (base + k * 32 + lane < wend) ? __ldcg(g.state + sb[k] + v[k]) : 0u;
-        uint32_t f = 0, ff = 0, dmin = kInf;
+        for (uint32_t k = 0; k < E; ++k)
+          cur[k] = (base + k * 32 + lane < wend) ? load_cur<OP>(rc, g.state + sb[k], v[k]) : 0u;
+        uint32_t f = 0, ff = 0, dmin = kInf, vmask = 0, rr[E], ndv[E];
+#pragma unroll
+        for (uint32_t k = 0; k < E; ++k) vmask |= (base + k * 32 + lane < wend ? 1u : 0u) << k;
+        decide_n<OP, 4>(rc, g.state, g.stamp, op, sb, v, ov, wt, cur, vmask, rr, ndv);
 #pragma unroll
         for (uint32_t k = 0; k < E; ++k) {
-          if (base + k * 32 + lane < wend) {
-            uint32_t nd = 0;
-            const uint32_t r =
-                decide_route<OP>(op[k], g.state + sb[k], g.stamp + sb[k], v[k], ov[k], wt[k], cur[k], rc, sb[k], nd);
-            if (r == 1u) f |= 1u << k;
-            if (r == 2u) {
-              ff |= 1u << k;
-              dmin = min(dmin, nd);
-            }
-            if (V::kBatched && r != 0u) g.mark(oqs[k], rc.ep);
+          const uint32_t r = rr[k];
+          if (r == 1u) f |= 1u << k;
+          if (r == 2u) {
+            ff |= 1u << k;
+            dmin = min(dmin, ndv[k]);
           }
+          if (V::kBatched && r != 0u) g.mark(oqs[k], rc.ep);
         }
         push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
         if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, ff, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3], dmin);
@@ -1130,6 +1234,7 @@ __device__ __forceinline__ void bottom_up_round(const KParams& p, Smem<CTA>& sm,
       }
       if (found) {
         __stcg(p.state + v, L + 1u);
+        if (p.vis) atomicOr(p.vis + (v >> 5), 1u << (v & 31u));
         atomicAdd(&sm.mf_cta, static_cast<unsigned long long>(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
       }
     }
@@ -1193,6 +1298,19 @@ __device__ __forceinline__ void fill_state(uint32_t* state, uint32_t n, const ui
     for (uint32_t v = (n4 << 2) + tid; v < n; v += nthreads) __stcg(state + v, value(v));
   } else {
     for (uint32_t v = tid; v < n; v += nthreads) __stcg(state + v, value(v));
+  }
+}
+
+// SSSP initial values in the packed form: (dist << 32) | 0, dist = 0 at the
+// in-register sources, INF elsewhere. Round ids start at 1, so no vertex
+// looks pushed in round 1.
+__device__ __forceinline__ void fill_packed(unsigned long long* ds, uint32_t n, const uint32_t* srcs, uint32_t nsrc,
+                                            uint32_t tid, uint32_t nthreads) {
+  for (uint32_t v = tid; v < n; v += nthreads) {
+    uint32_t d = kInf;
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) d = (i < nsrc && srcs[i] == v) ? 0u : d;
+    __stcg(ds + v, static_cast<unsigned long long>(d) << 32);
   }
 }
 
@@ -1271,16 +1389,26 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
 #pragma unroll
     for (uint32_t i = 0; i < 8; ++i) srcs[i] = (small && i < init_n) ? __ldcg(p.init_items + i) : kInf;
     if (small) ns = init_n;
-    fill_state<OP>(p.state, p.n, srcs, ns, blockIdx.x * CTA + threadIdx.x, gridDim.x * CTA);
+    if (OP == OP_SSSP && p.ds != nullptr) fill_packed(p.ds, p.n, srcs, ns, blockIdx.x * CTA + threadIdx.x, gridDim.x * CTA);
+    else fill_state<OP>(p.state, p.n, srcs, ns, blockIdx.x * CTA + threadIdx.x, gridDim.x * CTA);
     if (OP != OP_CC && !small) {
       ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
       if (ok) {
         for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < init_n; i += gridDim.x * CTA) {
           const uint32_t s = p.init_items ? __ldcg(p.init_items + i) : i;
-          if (s < p.n) __stcg(p.state + s, 0u);
+          if (s >= p.n) continue;
+          if (OP == OP_SSSP && p.ds != nullptr) __stcg(p.ds + s, 0ull);
+          else __stcg(p.state + s, 0u);
         }
       }
     }
+  } else if (OP == OP_SSSP && p.ds != nullptr) {
+    // the caller's initial distances, round id 0
+    for (uint32_t v = blockIdx.x * CTA + threadIdx.x; v < p.n; v += gridDim.x * CTA)
+      __stcg(p.ds + v, static_cast<unsigned long long>(__ldcg(p.state + v)) << 32);
+  }
+  if (OP == OP_BFS && p.vis != nullptr) {
+    for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < (p.n + 31u) >> 5; i += gridDim.x * CTA) __stcg(p.vis + i, 0u);
   }
   if (ok) ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
   trace_round(p.trace, p.trace_cap, 0, init_n, 0);
@@ -1321,6 +1449,9 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     rc.changes = nullptr;
     rc.mf = dopt ? &sm.mf_cta : nullptr;
     rc.row_ptr = p.row_ptr;
+    rc.vis = OP == OP_BFS ? p.vis : nullptr;
+    rc.ds = OP == OP_SSSP ? p.ds : nullptr;
+    rc.dsr = r + 1u;
     const uint32_t ftarget = split ? (fb ^ 1u) : fb;  // far list this round pushes to
     rc.far_out = Out{ftarget ? p.far[1] : p.far[0], &st->far_tail[ftarget], p.far_cap, &st->err};
     if (threadIdx.x == 0) {
@@ -1332,7 +1463,9 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
       sm.big_appended = 0;
       sm.far_min_cta = kInf;
       sm.mf_cta = 0;
-      if (dopt && blockIdx.x == 0) st->mf[(r + 2) % 3] = 0;
+      // mf[(r + 2) % 3] is still being read by CTAs that just left the last
+      // barrier; mf[(r + 1) % 3] was read by every CTA before it arrived there
+      if (dopt && blockIdx.x == 0) st->mf[(r + 1) % 3] = 0;
     }
     if (split) {
       split_far<OP, CTA>(g, sm, rc, fb ? p.far[1] : p.far[0], far_n, lim_old, limit);
@@ -1410,6 +1543,11 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     }
     in_n = min(last_out, p.cap);
   }
+  if (OP == OP_SSSP && p.ds != nullptr) {
+    // every round ended at a barrier that all CTAs passed: the words are final
+    for (uint32_t v = blockIdx.x * CTA + threadIdx.x; v < p.n; v += gridDim.x * CTA)
+      __stcg(p.state + v, static_cast<uint32_t>(__ldcg(p.ds + v) >> 32));
+  }
   const unsigned long long esum = cta_sum_u64<CTA>(sm, edges);
   persistent_exit<CTA>(sm, st, ok, rounds, last_out, ep0, esum, nullptr, 0);
 }
@@ -1453,6 +1591,9 @@ __device__ __forceinline__ void cc_jump_persistent(const KParams& p, Smem<CTA>& 
     rc.changes = &sm.round_pushes;  // the barrier publishes the grid's sum
     rc.mf = nullptr;
     rc.row_ptr = p.row_ptr;
+    rc.vis = nullptr;
+    rc.ds = nullptr;
+    rc.dsr = 0;
     if (threadIdx.x == 0) {
       if (blockIdx.x == 0) {
         st->tail[(r + 2) % 3] = 0;
@@ -1519,6 +1660,9 @@ __device__ __forceinline__ void invoke_round(const KParams& p, const RoundArgs& 
   rc.changes = nullptr;
   rc.mf = nullptr;
   rc.row_ptr = p.row_ptr;
+  rc.vis = nullptr;
+  rc.ds = nullptr;
+  rc.dsr = 0;
   uint32_t edges = 0, any_true = 0, any_false = 0;
   round_body<OP, CTA, RED>(g, sm, rc, edges, any_true, any_false);
   const int t = __syncthreads_or(any_true != 0);
@@ -1612,6 +1756,9 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
     rc.changes = nullptr;
     rc.mf = nullptr;
     rc.row_ptr = nullptr;
+    rc.vis = nullptr;
+    rc.ds = nullptr;
+    rc.dsr = 0;
     if (threadIdx.x == 0) {
       if (blockIdx.x == 0) {
         st->tail[(r + 2) % 3] = 0;

@@ -29,6 +29,10 @@ struct irgl_ctx {
   uint32_t ws_far_n = 0;
   uint32_t* ws_stamp = nullptr;  // SSSP/CC push dedup stamps
   uint32_t ws_stamp_n = 0;
+  uint32_t* ws_vis = nullptr;    // persistent BFS visited bitmap
+  uint32_t ws_vis_words = 0;
+  unsigned long long* ws_ds = nullptr;  // persistent SSSP packed (dist, round id) words
+  uint32_t ws_ds_n = 0;
   uint32_t* ws_state = nullptr;  // result buffer of irgl_run with a host output
   uint32_t ws_state_n = 0;
   irgl_worklist* run_wl = nullptr;  // sources of irgl_run
@@ -82,7 +86,8 @@ irgl_tuning default_tuning();
 irgl_status resolve_tuning(const irgl_tuning* in, irgl_tuning* out);
 irgl_status read_status(irgl_ctx* ctx, DevStatus* out);
 void reset_status(irgl_ctx* ctx);
-irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool need_far = false);
+irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool need_far = false,
+                             bool need_vis = false, bool need_ds = false);
 uint32_t big_capacity(uint64_t n);
 cudaError_t alloc_big(uint32_t cap, uint4** e, unsigned long long** off);
 int occupancy(irgl_ctx* ctx, int kind, uint32_t op, uint32_t cta, int red);

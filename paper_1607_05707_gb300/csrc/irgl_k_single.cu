@@ -1,4 +1,6 @@
 // Persistent cooperative Iterate kernels: BFS / SSSP / CC / pointer-jumping CC x CTA size.
+#include <algorithm>
+
 #include "irgl_launch.h"
 
 namespace irgl {
@@ -38,13 +40,42 @@ cudaError_t launch_op(uint32_t cta, uint32_t grid, const KParams& p, cudaStream_
   return cudaErrorInvalidValue;
 }
 
+// Resident CTAs per SM, after asking for the smallest shared-memory carveout
+// that keeps them all resident: the rest of the SM's 256 KB stays L1, which
+// caches the row offsets and (with the BFS bitmap) the visited bits. The
+// carveout is kept only if the occupancy calculator still gives the same
+// number of CTAs (the persistent grid is sized from it).
+template <class K>
+cudaError_t occ_prefer_l1(K kern, int cta, int* nb) {
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, cta, 0);
+  if (e != cudaSuccess || *nb <= 0) return e;
+  cudaFuncAttributes fa;
+  int dev = 0, smem_sm = 0, reserved = 0;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess || smem_sm <= 0)
+    return cudaSuccess;  // keep the default carveout
+  const long long need = static_cast<long long>(*nb) * (static_cast<long long>(fa.sharedSizeBytes) + reserved);
+  const int pct = static_cast<int>(std::min<long long>(100, (need * 100 + smem_sm - 1) / smem_sm));
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess) {
+    cudaGetLastError();  // the refused hint's own error, not a sticky one
+    return cudaSuccess;
+  }
+  int nb2 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, kern, cta, 0) != cudaSuccess || nb2 != *nb) {
+    cudaGetLastError();
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, -1);
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, cta, 0);
+}
+
 template <uint32_t OP>
 cudaError_t occ_op(uint32_t cta, int* nb) {
   switch (cta) {
-    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_iterate<OP, 128>, 128, 0);
-    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_iterate<OP, 256>, 256, 0);
-    case 512: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_iterate<OP, 512>, 512, 0);
-    case 1024: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_iterate<OP, 1024>, 1024, 0);
+    case 128: return occ_prefer_l1(k_iterate<OP, 128>, 128, nb);
+    case 256: return occ_prefer_l1(k_iterate<OP, 256>, 256, nb);
+    case 512: return occ_prefer_l1(k_iterate<OP, 512>, 512, nb);
+    case 1024: return occ_prefer_l1(k_iterate<OP, 1024>, 1024, nb);
   }
   return cudaErrorInvalidValue;
 }

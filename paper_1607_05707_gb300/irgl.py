@@ -40,6 +40,8 @@ IRGL_VALIDATE = 0x4
 IRGL_IN_EDGES = 0x8
 IRGL_TUNE_NO_SPLIT = 0x1
 IRGL_TUNE_DIROPT = 0x2
+IRGL_TUNE_BITMAP = 0x4
+IRGL_TUNE_NO_PACKED = 0x8
 
 KERNELS = {"bfs": IRGL_BFS, "sssp": IRGL_SSSP, "cc": IRGL_CC, "cc_jump": IRGL_CC_JUMP}
 MODES = {"per_launch": IRGL_PER_LAUNCH, "persistent": IRGL_PERSISTENT}

@@ -30,6 +30,8 @@ SCHEDULES = [
     dict(cta_size=128, delta=16),                                 # SSSP near-far schedule
     dict(cta_size=256, warp_thresh=4, cta_thresh=16, delta=1),    # near-far, one distance per bucket
     dict(cta_size=512, delta=100000),                             # near-far bucket wider than any distance
+    dict(cta_size=256, flags=4 | 8),      # BFS visited bitmap, SSSP distances and stamps in two arrays
+    dict(cta_size=1024, warp_thresh=1 << 30, cta_thresh=1 << 30, flags=8),  # two-array SSSP through the scan bin
 ]
 
 
@@ -282,17 +284,19 @@ def test_errors_and_recovery(ctx):
     # worklist overflow: scratch worklists far too small
     ctx.debug_set(3, 4)
     for mode in MODES:
-        with pytest.raises(C.IrglError) as ei:
-            ctx.run("bfs", dg, s, mode=mode)
-        assert ei.value.status == C.IRGL_ERR_WL_OVERFLOW
+        for kernel in ("bfs", "sssp"):
+            with pytest.raises(C.IrglError) as ei:
+                ctx.run(kernel, dg, s, mode=mode)
+            assert ei.value.status == C.IRGL_ERR_WL_OVERFLOW
     ctx.debug_set(3, 0)
     check(ctx, "bfs", g, dg, s)
     # barrier timeout: one CTA never arrives, the others give up after 20 ms
     ctx.debug_set(1, 20000)
     ctx.debug_set(2, 1)
-    with pytest.raises(C.IrglError) as ei:
-        ctx.run("bfs", dg, s, mode="persistent")
-    assert ei.value.status == C.IRGL_ERR_BARRIER_TIMEOUT
+    for kernel in ("bfs", "sssp"):
+        with pytest.raises(C.IrglError) as ei:
+            ctx.run(kernel, dg, s, mode="persistent")
+        assert ei.value.status == C.IRGL_ERR_BARRIER_TIMEOUT
     ctx.debug_set(2, -1)
     ctx.debug_set(1, 0)
     check(ctx, "bfs", g, dg, s)
@@ -374,6 +378,25 @@ def test_bottom_up_every_round(ctx):
         dg.close()
     finally:
         ctx.debug_set(5, 0)
+
+
+def test_bfs_visited_bitmap(ctx):
+    """The persistent BFS visited bitmap (IRGL_TUNE_BITMAP = 4) gives the same
+    levels; it is cleared per launch, so a graph run after a larger one (whose
+    bits were all set) is not filtered by stale bits; vertex counts that are
+    not multiples of 32 end in a partial word."""
+    rng = np.random.default_rng(61)
+    big = inputs.rmat(15, 16, seed=62)
+    dbig = ctx.load(big)
+    for tuning in (dict(flags=4), None, dict(cta_size=1024, warp_thresh=2, cta_thresh=8, flags=4),
+                   dict(cta_size=128, warp_thresh=1 << 30, cta_thresh=1 << 30, flags=1 | 4), dict(flags=2 | 4)):
+        check(ctx, "bfs", big, dbig, inputs.sources(big, 1, seed=63), "persistent", tuning)
+        for n in (1, 31, 33, 1000 + 7):
+            g = tiny_graph(rng, n, min(1.0, 4.0 / n), bool(n % 2))
+            dg = ctx.load(g)
+            check(ctx, "bfs", g, dg, np.array([int(rng.integers(0, n))], np.uint32), "persistent", tuning)
+            dg.close()
+    dbig.close()
 
 
 # ----------------------------------------------------------------------------- configuration sizes
