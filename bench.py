@@ -56,6 +56,10 @@ def parse_args():
     ap.add_argument("--verify", type=int, default=32, help="serve: queries checked against the oracle")
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (rmat20 workload)")
     ap.add_argument("--mesh-side", type=int, default=4096)
+    ap.add_argument("--cc", choices=["label", "jump"], default="label",
+                    help="mesh: CC by min-label propagation (the Iterate of the paper's CC) or pointer jumping")
+    ap.add_argument("--cc-delta", type=int, default=1,
+                    help="mesh, label CC: near-far width on labels (1: smallest label first; 0: plain rounds)")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -181,8 +185,11 @@ def load_workload(args):
         meta = dict(V=g.n, m=g.m, sources=1)
     elif args.workload == "mesh":
         g, srcs = inputs.workload_mesh(args.mesh_side)
-        kernels = ("bfs",)
-        name = f"mesh{args.mesh_side}: {args.mesh_side}^2 mesh (1% edges deleted, 0.1% extra edges r<=8) BFS, source 0"
+        cc = "cc_jump" if args.cc == "jump" else "cc"
+        kernels = ("bfs", cc)
+        name = (f"mesh{args.mesh_side}: {args.mesh_side}^2 mesh (1% edges deleted, 0.1% extra edges r<=8) BFS from "
+                f"source 0 + CC ({'pointer jumping' if args.cc == 'jump' else 'min-label propagation'}"
+                f"{f', near-far delta {args.cc_delta}' if args.cc != 'jump' and args.cc_delta else ''})")
         meta = dict(V=g.n, m=g.m, sources=1)
     else:
         g, srcs = inputs.workload_rmat20(nsrc=64, scale=args.scale)
@@ -204,6 +211,8 @@ def alg_bytes(kernel: str, n: int, R: int, mR: int) -> int:
     b = 4 * n + 20 * R + 8 * mR  # init + (row_ptr pair, pop, push, state write) per reached + (col, dst state) per edge
     if kernel == "sssp":
         b += 4 * mR + 4 * R  # weights + dedup stamp
+    elif kernel.startswith("cc"):
+        b += 4 * R  # dedup stamp
     return b
 
 
@@ -246,7 +255,7 @@ def cpu_oracle_sample(g, srcs, kernels, budget_s: float):
     for s in srcs:
         for k in kernels:
             t0 = time.perf_counter()
-            res = oracle.run(k, g, np.array([s], np.uint32))
+            res = oracle.run("cc" if k.startswith("cc") else k, g, None if k.startswith("cc") else np.array([s], np.uint32))
             dt = time.perf_counter() - t0
             t_total += dt
             edges += reached_stats(g, res)[1]
@@ -272,7 +281,7 @@ def run_reference(args, world, rank):
         e = 0
         t0 = time.perf_counter()
         for k in kernels:
-            e += reached_stats(g, oracle.run(k, g, s))[1]
+            e += reached_stats(g, oracle.run("cc" if k.startswith("cc") else k, g, None if k.startswith("cc") else s))[1]
         return time.perf_counter() - t0, e
 
     for i in range(args.warmup):
@@ -318,6 +327,8 @@ def run_gpu(args, world, rank, local):
         t = dict(tuning or {})
         if args.diropt and k == "bfs":
             t["flags"] = int(t.get("flags", 0)) | 2
+        if k == "cc" and args.cc_delta and "delta" not in t:
+            t["delta"] = args.cc_delta
         ktune[k] = t or None
     wls = []
     for s in srcs:
@@ -326,6 +337,9 @@ def run_gpu(args, world, rank, local):
         wls.append(wl)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
     torch.cuda.synchronize(dev)
+
+    def init(k, j):
+        return None if k.startswith("cc") else wls[j]  # CC: Iterate over every vertex
 
     def launch_step(j):
         """One step: BFS (and SSSP) from source j, each one persistent launch, bracketed by events."""
@@ -336,7 +350,7 @@ def run_gpu(args, world, rank, local):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.iterate_async(k, dg, wls[j], out[k], tuning=ktune[k])
+            ctx.iterate_async(k, dg, init(k, j), out[k], tuning=ktune[k])
             e1.record(stream)
             ev[k] = (e0, e1)
         ctx.sync()
@@ -350,13 +364,13 @@ def run_gpu(args, world, rank, local):
     counts, scanned = {}, {k: 0 for k in kernels}
     for j in sorted(set(used)):
         for k in kernels:
-            ctx.iterate_async(k, dg, wls[j], out[k], tuning=ktune[k])
+            ctx.iterate_async(k, dg, init(k, j), out[k], tuning=ktune[k])
             scanned[k] += ctx.sync()["edges_scanned"]
             counts[(j, k)] = reached_stats(g, as_u32(out[k])[: g.n])
     if args.trace and rank == 0:
         C.irgl_trace_enable(ctx.handle, 1 << 16)
         for k in kernels:
-            ctx.iterate_async(k, dg, wls[used[0]], out[k], tuning=ktune[k])
+            ctx.iterate_async(k, dg, init(k, used[0]), out[k], tuning=ktune[k])
             st = ctx.sync()
             t, a, o = C.irgl_trace_read(ctx.handle)
             print(f"# trace {k} source {srcs[used[0]]}: rounds={st['rounds']} total_us={(int(t[-1]) - int(t[0])) / 1e3:.1f}",
@@ -398,7 +412,7 @@ def run_gpu(args, world, rank, local):
                              us_per_launch=1e6 * tk / nk,
                              work_inefficiency=scanned[k] / max(1, sum(counts[(j, k)][1] for j in set(used))))
     dom = max(kernels, key=lambda k: per_kernel[k]["time_s"])
-    kname = {"bfs": "k_iterate<BFS>", "sssp": "k_iterate<SSSP>", "cc": "k_iterate<CC>"}[dom]
+    kname = {"bfs": "k_iterate<BFS>", "sssp": "k_iterate<SSSP>", "cc": "k_iterate<CC>", "cc_jump": "k_iterate<CCJ>"}[dom]
     pk = per_kernel[dom]
     traffic = measured_traffic(kname)
     roofline = {"bound": "hbm", "achieved": round(pk["achieved_gbs"], 2), "peak": hbm, "unit": "GB/s",
@@ -417,7 +431,7 @@ def run_gpu(args, world, rank, local):
         s = np.array([srcs[(args.warmup + i) % len(srcs)]], np.uint32)
         for k in kernels:
             t0 = time.perf_counter()
-            ctx.run_host(k, dg, s, out=host_out, tuning=ktune[k])
+            ctx.run_host(k, dg, None if k.startswith("cc") else s, out=host_out, tuning=ktune[k])
             e2e_t += time.perf_counter() - t0
             e2e_edges += reached_stats(g, host_out)[1]
     e2e_max = max_over_ranks(e2e_t, world, dev)

@@ -88,9 +88,11 @@ typedef struct {
   uint32_t max_blocks;    /* upper bound on the grid; 0 = none */
   uint32_t flags;         /* IRGL_TUNE_NO_SPLIT: persistent kernels keep long lists in the CTA bin
                              instead of splitting their edges over the whole grid */
-  uint32_t delta;         /* persistent SSSP only: near-far bucket width. Improvements to a distance
-                             >= the current limit wait on a far list until the rounds below the
-                             limit drain; 0 = plain rounds (every improvement is pushed) */
+  uint32_t delta;         /* persistent SSSP and CC only: near-far bucket width. Improvements to a
+                             value (distance, label) >= the current limit wait on a far list until
+                             the rounds below the limit drain; 0 = plain rounds (every improvement
+                             is pushed). CC with delta = 1 floods the smallest label first, so
+                             each vertex mostly takes its final label once */
 } irgl_tuning;
 
 #define IRGL_TUNE_NO_SPLIT 0x1u

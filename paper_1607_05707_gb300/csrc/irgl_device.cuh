@@ -34,6 +34,11 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Operator ids (OP_RUNTIME: taken per query from the batch descriptor).
 enum : uint32_t { OP_BFS = 0, OP_SSSP = 1, OP_CC = 2, OP_RUNTIME = 3, OP_CCJ = 4 };
+
+// Operators whose values can be scheduled near-far (smallest first): SSSP
+// distances and min-label CC labels.
+template <uint32_t OP>
+constexpr bool kNearFarOp = OP == OP_SSSP || OP == OP_CC;
 enum : int { RED_NONE = 0, RED_ANY = 1, RED_ALL = 2 };
 // Device error codes (first one wins).
 enum : uint32_t {
@@ -80,7 +85,7 @@ struct alignas(128) DevStatus {
   uint32_t pad5[28];
   // per-round bitmaps of the batched queries that pushed (folded into qlast)
   uint32_t qmask[2][32];
-  // SSSP near-far: sizes of the two far lists and the smallest distance pushed to each
+  // near-far (SSSP, CC): sizes of the two far lists and the smallest value pushed to each
   uint32_t far_tail[2];
   uint32_t far_min[2];
   uint32_t pad6[4];
@@ -137,7 +142,7 @@ struct KParams {
   unsigned long long* trace;   // optional per-round trace: {end time ns, (in_n << 32) | out_n}
   uint32_t trace_cap;          // rounds the trace can hold
   BigList big;
-  // SSSP near-far schedule (delta = 0: off)
+  // near-far schedule, SSSP and CC (delta = 0: off)
   uint32_t* far[2];
   uint32_t far_cap;
   uint32_t* far_stamp;
@@ -567,7 +572,7 @@ struct RoundCtx {
   Tune tn;
   BigList big;                    // cap 0: long lists stay in the CTA bin
   unsigned long long* big_ctr;
-  // SSSP near-far: improvements to a distance >= limit go to the far list
+  // near-far (SSSP, CC): improvements to a value >= limit go to the far list
   uint32_t limit;                 // kInf: every improvement goes to `out`
   Out far_out;
   uint32_t* far_stamp;
@@ -593,7 +598,7 @@ __device__ __forceinline__ uint32_t load_cur(const RoundCtx& rc, const uint32_t*
   return __ldcg(state + v);
 }
 
-// decide() with the SSSP near-far routing: 0 = no push, 1 = push to this
+// decide() with the near-far routing (SSSP, CC): 0 = no push, 1 = push to this
 // round's out-worklist, 2 = push to the far list. Near pushes dedup on the
 // round stamp, far pushes on the phase stamp, so a vertex improved first above
 // and then below the limit within one round still reaches the out-worklist.
@@ -622,8 +627,8 @@ __device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state
     const unsigned long long old = atomicMin(rc.ds + v, (static_cast<unsigned long long>(nd) << 32) | rc.dsr);
     return (nd < static_cast<uint32_t>(old >> 32) && static_cast<uint32_t>(old) != rc.dsr) ? 1u : 0u;
   }
-  if (OP != OP_SSSP || rc.limit == kInf) return decide<OP>(op_rt, state, stamp, v, val, wt, cur, rc.ep) ? 1u : 0u;
-  const uint32_t nd = val + static_cast<uint32_t>(wt);
+  if (!kNearFarOp<OP> || rc.limit == kInf) return decide<OP>(op_rt, state, stamp, v, val, wt, cur, rc.ep) ? 1u : 0u;
+  const uint32_t nd = OP == OP_SSSP ? val + static_cast<uint32_t>(wt) : val;
   if (nd >= cur) return 0u;
   const uint32_t old = atomicMin(state + v, nd);
   if (nd >= old) return 0u;
@@ -635,14 +640,14 @@ __device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state
 // The operator on N edges of one lane at once. Every atomic whose result
 // decides a push is issued before any of those results is read, so the N L2
 // round trips overlap instead of following one another. Same outcome as
-// decide_route edge by edge (which near-far SSSP and pointer-jumping CC keep
+// decide_route edge by edge (which near-far rounds and pointer-jumping CC keep
 // using). `state`/`stamp` are array bases, edge k's vertex is sb[k] + v[k].
 template <uint32_t OP, int N>
 __device__ __forceinline__ void decide_n(const RoundCtx& rc, uint32_t* state, uint32_t* stamp,
                                          const uint32_t (&op)[N], const uint32_t (&sb)[N], const uint32_t (&v)[N],
                                          const uint32_t (&val)[N], const int32_t (&wt)[N], const uint32_t (&cur)[N],
                                          uint32_t valid, uint32_t (&r)[N], uint32_t (&nd)[N]) {
-  if (OP == OP_CCJ || (OP == OP_SSSP && rc.limit != kInf)) {
+  if (OP == OP_CCJ || (kNearFarOp<OP> && rc.limit != kInf)) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       nd[k] = 0;
@@ -750,7 +755,7 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
       r = decide_route<OP>(op, state, stamp, v, val, wt, load_cur<OP>(rc, state, v), rc, sb, nd);
     }
     push1<CTA>(sm, rc.out, r == 1u, sb + v);
-    if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, r == 2u ? 1u : 0u, sb + v, 0u, 0u, 0u, nd);
+    if (kNearFarOp<OP>) push_far4<CTA>(sm, rc.far_out, r == 2u ? 1u : 0u, sb + v, 0u, 0u, 0u, nd);
     any |= r != 0;
   };
   scalar(beg + rank, a);
@@ -775,14 +780,14 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (rr[k] == 1u) fn |= 1u << k;
-        if (OP == OP_SSSP && rr[k] == 2u) {
+        if (kNearFarOp<OP> && rr[k] == 2u) {
           ff |= 1u << k;
           dmin = min(dmin, ndv[k]);
         }
       }
     }
     push4<CTA>(sm, rc.out, fn, sb + c.x, sb + c.y, sb + c.z, sb + c.w);
-    if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, ff, sb + c.x, sb + c.y, sb + c.z, sb + c.w, dmin);
+    if (kNearFarOp<OP>) push_far4<CTA>(sm, rc.far_out, ff, sb + c.x, sb + c.y, sb + c.z, sb + c.w, dmin);
     any |= (fn | ff) != 0;
     if (GROUP == CTA) {
       // the predicate is taken at the barrier, when every warp's pushes are in
@@ -949,7 +954,7 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
       }
     }
     push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
-    if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, ff, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3], dmin);
+    if (kNearFarOp<OP>) push_far4<CTA>(sm, rc.far_out, ff, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3], dmin);
     pushed |= (f | ff) != 0;
   }
 
@@ -1177,7 +1182,7 @@ __device__ __forceinline__ void big_phase(const V& g, Smem<CTA>& sm, const Round
           if (V::kBatched && r != 0u) g.mark(oqs[k], rc.ep);
         }
         push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
-        if (OP == OP_SSSP) push_far4<CTA>(sm, rc.far_out, ff, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3], dmin);
+        if (kNearFarOp<OP>) push_far4<CTA>(sm, rc.far_out, ff, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3], dmin);
       }
       pos = wend;
       i0 += lim;
@@ -1245,7 +1250,7 @@ __device__ __forceinline__ void bottom_up_round(const KParams& p, Smem<CTA>& sm,
   flush_stage<CTA>(sm, rc.out);
 }
 
-// SSSP near-far phase change: every item of the finished phase's far list is
+// Near-far phase change: every item of the finished phase's far list is
 // checked against its current distance d. d < lim_old: it was improved below
 // the old limit after it was pushed far, which pushed it to an out-worklist
 // then, so it is dropped. lim_old <= d < lim_new: it joins this round's
@@ -1413,10 +1418,11 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   if (ok) ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
   trace_round(p.trace, p.trace_cap, 0, init_n, 0);
 
-  // SSSP near-far schedule: improvements to a distance >= limit wait on a far
-  // list; when a round pushes nothing below the limit, a split round raises the
-  // limit and releases the far items below it (delta = 0: plain rounds).
-  const bool nf = OP == OP_SSSP && p.delta != 0 && p.far_stamp != nullptr;
+  // Near-far schedule (SSSP distances, CC labels): improvements to a value >=
+  // limit wait on a far list; when a round pushes nothing below the limit, a
+  // split round raises the limit and releases the far items below it (delta =
+  // 0: plain rounds).
+  const bool nf = kNearFarOp<OP> && p.delta != 0 && p.far_stamp != nullptr;
   uint32_t limit = nf ? p.delta : kInf, lim_old = 0;
   uint32_t fb = 0;        // far list receiving pushes in the current phase
   uint32_t phase = ep0;   // far-list dedup id of the current phase

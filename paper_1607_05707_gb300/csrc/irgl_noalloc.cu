@@ -40,10 +40,9 @@ struct NoAllocScratch {
   uint32_t items[2][kNoAllocMaxN];
   uint4 big_e[kNoAllocBigCap];
   unsigned long long big_off[kNoAllocBigCap];
-  uint32_t vis[kNoAllocMaxN / 32];  // visited bitmap, cleared by the kernel's prologue
 };
 
-// about 1 KiB status + 128 B + 8 MiB worklists + 1.5 MiB big list + 128 KiB bitmap: about 9.7 MiB per device.
+// about 1 KiB status + 128 B + 8 MiB worklists + 1.5 MiB big list: about 9.6 MiB per device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
 __global__ void __launch_bounds__(kNoAllocCta, MinBlocks<kNoAllocCta>::value) k_bfs_noalloc(KParams p) {
@@ -136,7 +135,6 @@ extern "C" irgl_status irgl_bfs_noalloc(int device, void* cuda_stream, uint32_t 
   p.trace = nullptr;
   p.trace_cap = 0;
   p.big = BigList{sc->big_e, sc->big_off, kNoAllocBigCap};
-  p.vis = sc->vis;
 
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(d.grid);

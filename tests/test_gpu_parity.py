@@ -32,6 +32,7 @@ SCHEDULES = [
     dict(cta_size=512, delta=100000),                             # near-far bucket wider than any distance
     dict(cta_size=256, flags=4 | 8),      # BFS visited bitmap, SSSP distances and stamps in two arrays
     dict(cta_size=1024, warp_thresh=1 << 30, cta_thresh=1 << 30, flags=8),  # two-array SSSP through the scan bin
+    dict(cta_size=512, warp_thresh=4, cta_thresh=32, delta=8),    # near-far through small bins
 ]
 
 
@@ -179,6 +180,39 @@ def test_cc_jump_many_components(ctx, tuning):
     check(ctx, "cc_jump", sym, ds, None, "persistent", tuning)
     check(ctx, "cc", sym, ds, None, "persistent", tuning)
     ds.close()
+
+
+@pytest.mark.parametrize("delta", [1, 7, 1000, 1 << 30])
+def test_cc_near_far(ctx, delta):
+    """Min-label CC under the near-far schedule (labels below the limit first):
+    same labels on many-component meshes, hub graphs and tiny graphs; with
+    delta = 1 the smallest label floods first, so a mostly connected mesh is
+    scanned about twice (round 0 plus the flood), not once per label change."""
+    tn = dict(delta=delta)
+    g = inputs.mesh(200, 170, seed=13, del_frac=0.45, extra_frac=0.01, radius=8)
+    dg = ctx.load(g)
+    check(ctx, "cc", g, dg, None, "persistent", tn)
+    check(ctx, "cc", g, dg, None, "persistent", dict(tn, cta_size=1024, warp_thresh=2, cta_thresh=8))
+    dg.close()
+    r = inputs.rmat(13, 8, seed=15, weights=False)
+    u = np.repeat(np.arange(r.n), np.diff(r.row_ptr.astype(np.int64)))
+    sym = inputs.csr_from_edges(r.n, np.concatenate([u, r.col]), np.concatenate([r.col, u]), symmetric=True)
+    ds = ctx.load(sym)
+    check(ctx, "cc", sym, ds, None, "persistent", dict(tn, cta_size=256))
+    ds.close()
+    rng = np.random.default_rng(16 + delta % 97)
+    for trial in range(6):
+        n = int(rng.integers(1, 120))
+        t = tiny_graph(rng, n, float(rng.choice([0.01, 0.05])), True)
+        dt = ctx.load(t)
+        check(ctx, "cc", t, dt, None, "persistent", tn)
+        dt.close()
+    m = inputs.mesh(300, 257, seed=9, del_frac=0.01, extra_frac=0.001, radius=8)
+    dm = ctx.load(m)
+    st = check(ctx, "cc", m, dm, None, "persistent", tn)
+    if delta == 1:
+        assert st["edges_scanned"] <= 3 * m.m
+    dm.close()
 
 
 def test_cc_jump_mesh4096_full(ctx):
@@ -417,6 +451,14 @@ def test_rmat20_bfs_sssp_full(ctx, mode):
         one = np.array([s], np.uint32)
         check(ctx, "bfs", g, dg, one, mode)
         check(ctx, "sssp", g, dg, one, mode)
+    dg.close()
+
+
+def test_mesh4096_cc_near_far_full(ctx):
+    g, _ = inputs.workload_mesh(4096)
+    dg = ctx.load(g, validate=False)
+    st = check(ctx, "cc", g, dg, None, "persistent", dict(delta=1))
+    assert st["edges_scanned"] <= 3 * g.m
     dg.close()
 
 
