@@ -1011,6 +1011,23 @@ __device__ __forceinline__ void st_release_gpu_u64(unsigned long long* p, unsign
   asm volatile("st.release.gpu.global.u64 [%0], %1;" : : "l"(p), "l"(v) : "memory");
 }
 
+// Barrier arrival. Default: one acquire-release atomic (it publishes this CTA's
+// writes, which bar.sync ordered before it, and lets the last arrival see
+// every earlier CTA's). IRGL_BARRIER_FENCES: the older form, a relaxed atomic
+// between two full fences.
+__device__ __forceinline__ unsigned long long arrive_add(unsigned long long* p, unsigned long long v) {
+#ifdef IRGL_BARRIER_FENCES
+  __threadfence();
+  const unsigned long long old = atomicAdd(p, v);
+  __threadfence();
+  return old;
+#else
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+#endif
+}
+
 // SyncRunningThreads (Sec. 3.4): valid only because the launch is cooperative,
 // so every CTA is resident. Each CTA arrives with one 64-bit atomic that also
 // carries the out-worklist slots it reserved this round and whether it
@@ -1042,23 +1059,22 @@ __device__ __forceinline__ bool grid_barrier(Smem<CTA>& sm, DevStatus* st, uint3
         st->big_ctr = 0;
       }
     } else {
-      __threadfence();
       const uint32_t err_seen = __ldcg(&st->err);
-      const unsigned long long old = atomicAdd(&st->arrive, mine);
+      const unsigned long long old = arrive_add(&st->arrive, mine);
       const unsigned long long total = old + mine;
       if ((total & 0xFFFFull) == gridDim.x) {
-        // last arrival: every CTA's pushes and big-list appends are in
+        // last arrival: every CTA's pushes and big-list appends are in (and
+        // visible: its atomic acquired them)
         out = static_cast<uint32_t>(total >> 32);
         flags = err_seen & 0x7Fu;
         if (with_big && ((total >> 16) & 0xFFFFull) != 0) {
-          __threadfence();
           big = __ldcg(&st->big_ctr);
           flags |= kRelBigFlag;
           st->big_pub = big;
           st->big_ctr = 0;  // the next appends come after the big phase
         }
         st->arrive = 0;
-        __threadfence();
+        // the release store orders everything above (and all it acquired) before it
         st_release_gpu_u64(&st->rel, (static_cast<unsigned long long>(gen) << 40) |
                                           (static_cast<unsigned long long>(flags) << 32) | out);
       } else {
@@ -1082,7 +1098,8 @@ __device__ __forceinline__ bool grid_barrier(Smem<CTA>& sm, DevStatus* st, uint3
           }
         }
       }
-      __threadfence();
+      // no fence here: the acquire load above orders this thread's later
+      // accesses, and the bar.sync below orders the other threads' after it
     }
     sm.flag = ok;
     sm.pub_out = out;
