@@ -63,6 +63,7 @@ def parse_args():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-per-launch", action="store_true", help="skip the per-launch (host loop) BFS comparison")
     ap.add_argument("--tuning", type=str, default="", help="JSON irgl_tuning overrides")
     ap.add_argument("--trace", action="store_true", help="print a per-round trace of one query per kernel to stderr")
     ap.add_argument("--diropt", action="store_true",
@@ -216,15 +217,16 @@ def alg_bytes(kernel: str, n: int, R: int, mR: int) -> int:
     return b
 
 
-def source_sha() -> str:
+def source_sha(files) -> str:
+    """Hash of the source files a kernel is built from (in the order given)."""
     h = hashlib.sha256()
-    for p in sorted((ROOT / "paper_1607_05707_gb300" / "csrc").glob("irgl_*")):
-        h.update(p.read_bytes())
+    for name in files:
+        h.update((ROOT / "paper_1607_05707_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
 
 def measured_traffic(kernel_name: str):
-    """DRAM bytes per launch from a committed ncu capture, only if the kernel source is unchanged since."""
+    """DRAM bytes per launch from a committed ncu capture, only if the kernel's sources are unchanged since."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
         return None
@@ -233,7 +235,12 @@ def measured_traffic(kernel_name: str):
     except ValueError:
         return None
     ent = d.get(kernel_name)
-    if not ent or ent.get("source_sha") != source_sha():
+    if not ent or not ent.get("sources"):
+        return None
+    try:
+        if ent.get("source_sha") != source_sha(ent["sources"]):
+            return None
+    except OSError:
         return None
     return ent.get("bytes_per_launch")
 
@@ -361,11 +368,13 @@ def run_gpu(args, world, rank, local):
         launch_step(i % len(wls))
     # reached-vertex and edge counts per (source, kernel), taken from the results outside the timed region;
     # edges scanned (re-relaxations included) from the device counters, one query at a time
-    counts, scanned = {}, {k: 0 for k in kernels}
+    counts, scanned, rounds = {}, {k: 0 for k in kernels}, {}
     for j in sorted(set(used)):
         for k in kernels:
             ctx.iterate_async(k, dg, init(k, j), out[k], tuning=ktune[k])
-            scanned[k] += ctx.sync()["edges_scanned"]
+            st = ctx.sync()
+            scanned[k] += st["edges_scanned"]
+            rounds[(j, k)] = st["rounds"]
             counts[(j, k)] = reached_stats(g, as_u32(out[k])[: g.n])
     if args.trace and rank == 0:
         C.irgl_trace_enable(ctx.handle, 1 << 16)
@@ -381,6 +390,7 @@ def run_gpu(args, world, rank, local):
         C.irgl_trace_enable(ctx.handle, 0)
 
     rec = {k: [] for k in kernels}
+    nrounds = {k: [] for k in kernels}
     clocks = ClockSampler(local, enabled=(rank == 0 and not args.no_clocks))
     barrier(world)
     torch.cuda.synchronize(dev)
@@ -389,6 +399,7 @@ def run_gpu(args, world, rank, local):
         ev = launch_step(used[i])
         for k in kernels:
             rec[k].append((ev[k][0].elapsed_time(ev[k][1]) * 1e-3, *counts[(used[i], k)]))
+            nrounds[k].append(rounds[(used[i], k)])
     torch.cuda.synchronize(dev)
     barrier(world)
     t_wall = time.perf_counter() - t_wall0
@@ -407,9 +418,14 @@ def run_gpu(args, world, rank, local):
         tk = sum(t for (t, _, _) in rec[k])
         bk = sum(alg_bytes(k, g.n, R, mR) for (_, R, mR) in rec[k])
         nk = len(rec[k])
+        q_gteps = [mR / t / 1e9 for (t, _, mR) in rec[k]]
         per_kernel[k] = dict(time_s=tk, bytes=bk, launches=nk, achieved_gbs=bk / tk / 1e9,
                              gteps=sum(mR for (_, _, mR) in rec[k]) / tk / 1e9,
+                             gteps_median=statistics.median(q_gteps),
+                             gteps_harmonic=len(q_gteps) / sum(1.0 / x for x in q_gteps),
                              us_per_launch=1e6 * tk / nk,
+                             rounds_per_launch=sum(nrounds[k]) / nk,
+                             us_per_round=1e6 * tk / max(1, sum(nrounds[k])),
                              work_inefficiency=scanned[k] / max(1, sum(counts[(j, k)][1] for j in set(used))))
     dom = max(kernels, key=lambda k: per_kernel[k]["time_s"])
     kname = {"bfs": "k_iterate<BFS>", "sssp": "k_iterate<SSSP>", "cc": "k_iterate<CC>", "cc_jump": "k_iterate<CCJ>"}[dom]
@@ -437,6 +453,22 @@ def run_gpu(args, world, rank, local):
     e2e_max = max_over_ranks(e2e_t, world, dev)
     e2e_val = sum_over_ranks(e2e_edges, world, dev) / e2e_max / 1e9
 
+    # iteration outlining vs one launch per round (host loop), BFS from the first timed source
+    outlining = None
+    if "bfs" in kernels and not args.no_per_launch:
+        j = used[0]
+        t_pl = []
+        for rep_i in range(3):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            _, st = ctx.iterate("bfs", dg, wls[j], out["bfs"], mode="per_launch", tuning=ktune["bfs"])
+            t_pl.append(time.perf_counter() - t0)
+        t_pers = [t for (t, _, _), jj in zip(rec["bfs"], used) if jj == j]
+        outlining = {"kernel": "bfs", "rounds": st["rounds"], "per_launch_us": round(1e6 * min(t_pl), 1),
+                     "per_launch_launches": st["launches"],
+                     "persistent_us": round(1e6 * statistics.median(t_pers), 1),
+                     "speedup": round(min(t_pl) / statistics.median(t_pers), 2)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(g, srcs_all, kernels, args.cpu_budget)
@@ -459,6 +491,7 @@ def run_gpu(args, world, rank, local):
             "cpu_baseline": cpu,
             "clocks": clk,
             "wall_s_timed_region": round(t_wall, 4),
+            "outlining": outlining,
         }
         print(json.dumps(line), flush=True)
     for wl in wls:

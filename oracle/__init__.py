@@ -1,9 +1,9 @@
 """CPU oracle (TEST INFRASTRUCTURE ONLY).
 
 Plain serial CPU implementations of the fixed points that the GPU worklist
-kernels must reach: FIFO-queue BFS levels, binary-heap Dijkstra distances and
-union-find minimum-id component labels (``oracle.c``; each function there cites
-the definition it follows).
+kernels must reach: FIFO-queue BFS levels, binary-heap Dijkstra distances,
+union-find minimum-id component labels and the Kruskal minimum spanning forest
+(``oracle.c``; each function there cites the definition it follows).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
 (and its ``--impl reference`` arm) may import this package. The library under
@@ -54,6 +54,9 @@ def _load():
         lib.oracle_sssp.argtypes = [ctypes.c_uint32, u32p, u32p, i32p, ctypes.c_uint32, u32p, u32p]
         lib.oracle_cc.restype = ctypes.c_int
         lib.oracle_cc.argtypes = [ctypes.c_uint32, u32p, u32p, u32p]
+        lib.oracle_msf.restype = ctypes.c_int
+        lib.oracle_msf.argtypes = [ctypes.c_uint32, u32p, u32p, i32p, u32p, u32p, i32p, u32p,
+                                   ctypes.POINTER(ctypes.c_uint64)]
         _lib = lib
     return _lib
 
@@ -95,6 +98,23 @@ def cc(n: int, row_ptr, col) -> np.ndarray:
     out = np.empty(n, dtype=np.uint32)
     _check(_load().oracle_cc(n, _ptr(rp), _ptr(c), _ptr(out)), "oracle_cc")
     return out
+
+
+def msf(n: int, row_ptr, col, w) -> tuple[np.ndarray, int]:
+    """Minimum spanning forest under the key (w, min(u,v), max(u,v)): its edges as
+    rows (u, v, w) with u < v, in key order, and their total weight."""
+    rp, c = _u32(row_ptr), _u32(col)
+    ww = np.ascontiguousarray(w, dtype=np.int32)
+    cap = max(n - 1, 1)
+    ou, ov = np.empty(cap, dtype=np.uint32), np.empty(cap, dtype=np.uint32)
+    ow = np.empty(cap, dtype=np.int32)
+    cnt = ctypes.c_uint32(0)
+    tot = ctypes.c_uint64(0)
+    _check(_load().oracle_msf(n, _ptr(rp), _ptr(c), _ptr(ww, ctypes.c_int32), _ptr(ou), _ptr(ov),
+                              _ptr(ow, ctypes.c_int32), ctypes.byref(cnt), ctypes.byref(tot)), "oracle_msf")
+    k = cnt.value
+    edges = np.stack([ou[:k].astype(np.int64), ov[:k].astype(np.int64), ow[:k].astype(np.int64)], axis=1)
+    return edges.reshape(k, 3), int(tot.value)
 
 
 def run(kind: str, g, srcs=None) -> np.ndarray:

@@ -23,9 +23,15 @@
  *   oracle_cc   -- label[v] = smallest vertex id in v's connected component,
  *                  edges taken as undirected. Union-find (union by rank, path
  *                  halving), then the minimum id per root.
+ *   oracle_msf  -- minimum spanning forest (Sec. 3.3's Boruvka example computes
+ *                  it): the undirected edges {u, v} (u != v) of the CSR entries,
+ *                  ordered by the key (w, min(u,v), max(u,v)), which makes the
+ *                  forest unique (equal keys are copies of one edge). Kruskal:
+ *                  sort the keys, keep each edge that joins two union-find sets.
  *
  * Return values: 0 on success; -1 invalid argument (vertex id out of range,
- * negative weight); -2 out of memory; -3 a distance does not fit below INF.
+ * negative weight); -2 out of memory; -3 a distance does not fit below INF;
+ * -4 more forest edges than n - 1 (cannot happen for a forest).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -191,5 +197,80 @@ int oracle_cc(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, uint32_t
   free(parent);
   free(rank);
   free(minid);
+  return 0;
+}
+
+/* ---------------------------------------------------------------- minimum spanning forest */
+
+typedef struct {
+  int32_t w;
+  uint32_t u, v; /* u < v */
+} msf_edge;
+
+static int msf_key_cmp(const void* pa, const void* pb) {
+  const msf_edge* a = (const msf_edge*)pa;
+  const msf_edge* b = (const msf_edge*)pb;
+  if (a->w != b->w) return a->w < b->w ? -1 : 1;
+  if (a->u != b->u) return a->u < b->u ? -1 : 1;
+  if (a->v != b->v) return a->v < b->v ? -1 : 1;
+  return 0;
+}
+
+/* Kruskal's algorithm over the key order (w, min(u,v), max(u,v)). Writes the
+ * kept edges in key order (out_u < out_v; capacity n - 1 each), their number
+ * and the sum of their weights. */
+int oracle_msf(uint32_t n, const uint32_t* row_ptr, const uint32_t* col, const int32_t* w, uint32_t* out_u,
+               uint32_t* out_v, int32_t* out_w, uint32_t* count, uint64_t* total) {
+  uint64_t m = n ? row_ptr[n] : 0, k = 0, e;
+  uint32_t u, kept = 0;
+  uint64_t sum = 0;
+  msf_edge* edges;
+  uint32_t* parent;
+  *count = 0;
+  *total = 0;
+  if (n == 0) return 0;
+  edges = (msf_edge*)malloc(sizeof(msf_edge) * (size_t)(m ? m : 1));
+  parent = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n);
+  if (!edges || !parent) {
+    free(edges);
+    free(parent);
+    return -2;
+  }
+  for (u = 0; u < n; ++u) {
+    parent[u] = u;
+    for (e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+      uint32_t v = col[e];
+      if (v >= n || w[e] < 0) {
+        free(edges);
+        free(parent);
+        return -1;
+      }
+      if (v == u) continue; /* a self-loop joins nothing */
+      edges[k].w = w[e];
+      edges[k].u = u < v ? u : v;
+      edges[k].v = u < v ? v : u;
+      ++k;
+    }
+  }
+  qsort(edges, (size_t)k, sizeof(msf_edge), msf_key_cmp);
+  for (e = 0; e < k; ++e) {
+    uint32_t a = uf_find(parent, edges[e].u), b = uf_find(parent, edges[e].v);
+    if (a == b) continue; /* closes a cycle: every cycle edge before it is lighter */
+    if (kept + 1 >= n) { /* a forest on n vertices has at most n - 1 edges */
+      free(edges);
+      free(parent);
+      return -4;
+    }
+    parent[a > b ? a : b] = a < b ? a : b;
+    out_u[kept] = edges[e].u;
+    out_v[kept] = edges[e].v;
+    out_w[kept] = edges[e].w;
+    sum += (uint64_t)edges[e].w;
+    ++kept;
+  }
+  *count = kept;
+  *total = sum;
+  free(edges);
+  free(parent);
   return 0;
 }
