@@ -46,7 +46,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["rmat20", "grid64", "mesh", "batch256", "serve"], default="rmat20")
+    ap.add_argument("--workload", choices=["rmat20", "grid64", "mesh", "batch256", "serve", "msf"], default="rmat20")
+    ap.add_argument("--msf-graph", choices=["mesh", "rmat"], default="mesh",
+                    help="msf: the weighted 4096^2 mesh or a symmetrised R-MAT scale-20 graph")
+    ap.add_argument("--msf-lock", choices=["blocking", "ticket", "retry"], default="blocking")
     ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrival rate (queries/s)")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: arrival window (s)")
@@ -280,6 +283,8 @@ def cpu_oracle_sample(g, srcs, kernels, budget_s: float):
 def run_reference(args, world, rank):
     if rank != 0:
         return
+    if args.workload == "msf":
+        return run_reference_msf(args)
     g, srcs, kernels, name, meta = load_workload(args)
     import oracle
 
@@ -307,6 +312,29 @@ def run_reference(args, world, rank):
         "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                          "sample": f"each step = {'+'.join(kernels)} from one source, serial"},
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_msf(args):
+    import oracle
+
+    g, name = msf_graph(args)
+    oracle.msf(g.n, g.row_ptr, g.col, g.w)  # one warm-up run: a step is a whole Kruskal run
+    t_sum = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.msf(g.n, g.row_ptr, g.col, g.w)
+        t_sum += time.perf_counter() - t0
+    value = args.steps * g.m / t_sum / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "G input edges/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * t_sum / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": name, "V": g.n, "m": g.m, "parallelism": "rank 0 only (serial CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": "G input edges/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step = one Kruskal run on the whole graph, serial"},
+        "e2e": {"value": value, "unit": "G input edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -724,6 +752,107 @@ def run_serve(args, world, rank, local):
     srv.close()
 
 
+# ----------------------------------------------------------------------------- minimum spanning forest
+
+def msf_graph(args):
+    from paper_1607_05707_gb300 import inputs
+
+    if args.msf_graph == "rmat":
+        r, _ = inputs.workload_rmat20(nsrc=1, scale=args.scale)
+        u = np.repeat(np.arange(r.n), np.diff(r.row_ptr.astype(np.int64)))
+        g = inputs.csr_from_edges(r.n, np.concatenate([u, r.col]), np.concatenate([r.col, u]),
+                                  np.concatenate([r.w, r.w]), symmetric=True)
+        return g, f"msf-rmat{args.scale}: R-MAT scale {args.scale} (edges of both directions, w in [1,100])"
+    g, _ = inputs.workload_mesh(args.mesh_side, weights=True)
+    return g, f"msf-mesh{args.mesh_side}: {args.mesh_side}^2 mesh (1% edges deleted, 0.1% extra r<=8), w in [1,100]"
+
+
+def run_msf(args, world, rank, local):
+    """Minimum spanning forest by Boruvka (outlined Pipe: find_min with Atomic component locks, link,
+    pointer jumping); queries are whole graphs, so N GPUs run N replicas."""
+    import torch
+
+    from paper_1607_05707_gb300.api import Context
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g, name = msf_graph(args)
+    tuning = json.loads(args.tuning) if args.tuning else None
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context(local, stream)
+    dg = ctx.load(g, validate=False)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        ctx.msf(dg, lock=args.msf_lock, tuning=tuning)
+    clocks = ClockSampler(local, enabled=(rank == 0 and not args.no_clocks))
+    barrier(world)
+    times, st = [], None
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i)
+        torch.cuda.synchronize(dev)
+        _, st = ctx.msf(dg, lock=args.msf_lock, tuning=tuning)
+        times.append(st["device_ms"] * 1e-3)
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    t_step = max_over_ranks(sum(times) / len(times), world, dev)
+    value = sum_over_ranks(float(g.m), world, dev) / t_step / 1e9
+    # the same forest with a host loop launching each kernel invocation, and with the other lock forms
+    forms = {}
+    for lock in ("blocking", "ticket", "retry"):
+        _, s1 = ctx.msf(dg, lock=lock, tuning=tuning)
+        forms[lock] = {"ms": round(s1["device_ms"], 3), "locks": s1["locks"], "retries": s1["retries"]}
+    t0 = time.perf_counter()
+    _, spl = ctx.msf(dg, mode="per_launch", lock=args.msf_lock, tuning=tuning)
+    t_pl = time.perf_counter() - t0
+    # e2e: the call with the forest copied to host memory (inside the call), wall clock
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    edges, _ = ctx.msf(dg, lock=args.msf_lock, tuning=tuning)
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        t0 = time.perf_counter()
+        oracle.msf(g.n, g.row_ptr, g.col, g.w)
+        tc = time.perf_counter() - t0
+        cpu = {"value": g.m / tc / 1e9, "unit": "G input edges/s", "cores": 1, "kind": "oracle",
+               "sample": f"one Kruskal run on the whole graph ({g.m} CSR entries), {tc:.1f} s serial"}
+    hbm, peak_src = peaks()
+    nbytes = 12 * g.m + 16 * g.n  # col + w + comp[v] per CSR entry, row_ptr pair + comp[u] + record per vertex
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "G input edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": name, "V": g.n, "m": g.m, "lock": args.msf_lock,
+                       "mode": "persistent (outlined Pipe: find_min / link / jump in one cooperative launch)",
+                       "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write, outside)",
+                       "iterations": st["iterations"], "invocations": st["invocations"],
+                       "cta_size": st["cta_size"], "grid": st["grid"], "forest_edges": st["edges"],
+                       "forest_weight": st["weight"]},
+            "e2e": {"value": round(g.m / t_e2e / 1e9, 4), "unit": "G input edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 4 * int(len(edges))},
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "hbm", "achieved": round(nbytes / t_step / 1e9, 2), "peak": hbm, "unit": "GB/s",
+                         "frac": round(nbytes / t_step / 1e9 / hbm, 4), "traffic": measured_traffic("k_msf"),
+                         "kernel": "k_msf", "bytes_per_launch": int(nbytes),
+                         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
+            "lock_forms": forms,
+            "outlining": {"per_launch_us": round(1e6 * t_pl, 1), "per_launch_launches": spl["launches"],
+                          "persistent_us": round(1e6 * t_step, 1), "speedup": round(t_pl / t_step, 2)},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "wall_s_timed_region": round(t_wall, 4),
+        }
+        print(json.dumps(line), flush=True)
+    dg.close()
+    ctx.close()
+
+
 def main():
     args = parse_args()
     if args.warmup < 3:
@@ -735,6 +864,8 @@ def main():
         run_batch(args, world, rank, local)
     elif args.workload == "serve":
         run_serve(args, world, rank, local)
+    elif args.workload == "msf":
+        run_msf(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

@@ -43,6 +43,7 @@ typedef int irgl_status;
 #define IRGL_ERR_MAX_ROUNDS (-8)      /* Iterate stopped at max_rounds with work left */
 #define IRGL_ERR_NOT_READY (-9)       /* polled result not finished yet */
 #define IRGL_ERR_UNSUPPORTED (-10)    /* option not available for this kernel/mode */
+#define IRGL_ERR_LOCK_TIMEOUT (-11)   /* an Atomic section's lock wait hit its time limit */
 
 #define IRGL_INF 0xFFFFFFFFu
 
@@ -366,6 +367,59 @@ irgl_status irgl_server_destroy(irgl_server* s);
 irgl_status irgl_bfs_noalloc(int device, void* cuda_stream, uint32_t n, uint64_t m, const uint32_t* row_ptr,
                              const uint32_t* col, uint32_t src, uint32_t* level, uint32_t* rounds);
 
+/* ---------------------------------------------------------------- minimum spanning forest
+ * Boruvka's algorithm (Sec. 3.3, Listing "Find-Minimum-Cross-Component-Edge")
+ * as a Pipe of three kernels (Sec. 4.3): find_min (each vertex's lightest
+ * cross-component edge, merged into its component's record inside an Atomic
+ * section on the component's lock), link (record each component's edge, hook
+ * the component to the other one), and jump (pointer jumping until no vertex
+ * changes, Iterate Until !Any). The Pipe repeats until no component has a
+ * cross edge. Edges are ordered by the key (w, min(u,v), max(u,v)), so the
+ * forest is unique; parallel copies of an edge (same key) are interchangeable.
+ *
+ * Lock forms of the Atomic section (Sec. 3.3):
+ *   IRGL_LOCK_BLOCKING: atomicCAS retry loop, divergence-safe (the attempt and
+ *     the critical section share one branch);
+ *   IRGL_LOCK_TICKET:   ticket lock;
+ *   IRGL_LOCK_RETRY:    one attempt (Atomic ... Else): a vertex that misses the
+ *     lock goes to the retry worklist, and find_min is invoked again on that
+ *     list (in and retry swapped, out kept; Sec. 4.3) with contiguous blocks of
+ *     items per thread (Retry Backoff) until the list is empty.
+ * Lock waits (and one find_min's retries) are bounded by half the context's
+ * barrier time limit (1 s by default; test hook key 1) and end the call with
+ * IRGL_ERR_LOCK_TIMEOUT. Test hook key 6 makes one component's lock start
+ * held (never released).
+ *
+ * mode: IRGL_PERSISTENT outlines the whole Pipe into one cooperative launch
+ *   whose CTA size is chosen by the T_control rule (irgl_control_cta) over the
+ *   three kernels; IRGL_PER_LAUNCH launches each kernel invocation from a host
+ *   loop that reads the counters in between.
+ * g: loaded with IRGL_SYMMETRIC and weights (IRGL_ERR_NOT_SYMMETRIC,
+ *   IRGL_ERR_INVALID_ARG otherwise).
+ * out_edges: cap >= n - 1 uint32 CSR edge indices (device memory, or host
+ *   memory when out_on_host != 0), written in no particular order: one
+ *   direction (u -> v, either) of each forest edge. t: cta_size preference,
+ *   blocks_per_sm and max_blocks are used; NULL = defaults. stats: optional.
+ * Synchronises on the context's stream before returning. */
+typedef enum { IRGL_LOCK_BLOCKING = 0, IRGL_LOCK_TICKET = 1, IRGL_LOCK_RETRY = 2 } irgl_lock;
+
+typedef struct {
+  uint32_t edges;        /* forest edges written to out_edges */
+  uint32_t iterations;   /* Boruvka iterations (Pipe repetitions) */
+  uint64_t weight;       /* sum of the forest edges' weights */
+  uint32_t invocations;  /* kernel invocations inside the Pipe (find_min, retries, link, jump passes) */
+  uint32_t retries;      /* vertices pushed to the retry worklist (IRGL_LOCK_RETRY) */
+  uint32_t locks;        /* lock acquisitions (the rest passed the pre-lock weight test) */
+  uint32_t launches;     /* kernel launches */
+  uint32_t grid;
+  uint32_t cta_size;
+  float device_ms;       /* event time of the whole call on its stream */
+  uint32_t reserved;
+} irgl_msf_stats;
+
+irgl_status irgl_msf(irgl_ctx* ctx, irgl_graph* g, irgl_mode mode, irgl_lock lock, uint32_t* out_edges, uint32_t cap,
+                     int out_on_host, const irgl_tuning* t, irgl_msf_stats* stats);
+
 /* ---------------------------------------------------------------- test hooks
  * Fault injection on the host side only (no device fault is ever raised):
  *   key 1: barrier time limit in microseconds (0 = default 2 s)
@@ -375,7 +429,10 @@ irgl_status irgl_bfs_noalloc(int device, void* cuda_stream, uint32_t n, uint64_t
  *   key 3: override the capacity of the Iterate scratch worklists (0 = n).
  *   key 4: cap the big list of persistent Iterate launches (0 = default), so
  *          long lists beyond the cap take the CTA-bin path.
- *   key 5: 1 = direction-optimising BFS runs every round bottom-up. */
+ *   key 5: 1 = direction-optimising BFS runs every round bottom-up.
+ *   key 6: minimum spanning forest: the lock of this component (vertex id;
+ *          -1 = none) starts held and is never released, so its waits run
+ *          out and the call returns IRGL_ERR_LOCK_TIMEOUT. */
 irgl_status irgl_debug_set(irgl_ctx* ctx, int key, int64_t value);
 
 #ifdef __cplusplus

@@ -37,6 +37,7 @@ CUDA_UNITS = [
     "irgl_server.cu",
     "irgl_tune.cu",
     "irgl_noalloc.cu",
+    "irgl_msf.cu",
 ]
 HOST_UNITS: list[str] = []
 

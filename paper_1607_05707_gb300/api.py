@@ -146,6 +146,14 @@ class Context:
         return C.irgl_invoke(self.handle, C.KERNELS[kernel], g.handle, wl_in.handle, wl_out.handle, state.data_ptr(),
                              level, C.IRGL_REDUCE_ANY if reduce == "any" else C.IRGL_REDUCE_ALL, tuning)
 
+    def msf(self, g: Graph, mode: str = "persistent", lock: str = "blocking", tuning=None,
+            out: np.ndarray | None = None) -> tuple[np.ndarray, dict]:
+        """Minimum spanning forest (Boruvka): CSR indices of its edges (one direction each, any order)."""
+        cap = max(g.n - 1, 1)
+        buf = np.empty(cap, dtype=np.uint32) if out is None else out
+        st = C.irgl_msf(self.handle, g.handle, C.MODES[mode], C.LOCKS[lock], _np_ptr(buf), buf.size, 1, tuning)
+        return buf[: st["edges"]].copy(), st
+
     def init_state(self, kernel: str, g: Graph, initial: Worklist | None, state: torch.Tensor) -> None:
         C.irgl_init_state(self.handle, C.KERNELS[kernel], g.handle, None if initial is None else initial.handle,
                           state.data_ptr())

@@ -90,6 +90,8 @@ irgl_status status_from_device(const DevStatus& s) {
       return fail(IRGL_ERR_BARRIER_TIMEOUT, "grid barrier wait exceeded its time limit");
     case DERR_MAX_ROUNDS: return fail(IRGL_ERR_MAX_ROUNDS, "Iterate reached max_rounds with work left");
     case DERR_BAD_ITEM: return fail(IRGL_ERR_INVALID_ARG, "a worklist item is not a vertex of the graph");
+    case DERR_LOCK_TIMEOUT: return fail(IRGL_ERR_LOCK_TIMEOUT, "an Atomic section's lock wait exceeded its time limit");
+    case DERR_MSF_ITERS: return fail(IRGL_ERR_CUDA, "Boruvka's algorithm did not converge");
   }
   return fail(IRGL_ERR_CUDA, "unknown device error %u", s.err);
 }
@@ -345,6 +347,8 @@ irgl_status irgl_ctx_destroy(irgl_ctx* ctx) {
   cudaFree(ctx->ws_stamp);
   cudaFree(ctx->ws_vis);
   cudaFree(ctx->ws_ds);
+  cudaFree(ctx->msf_buf);
+  if (ctx->msf_host) cudaFreeHost(ctx->msf_host);
   cudaFree(ctx->ws_far[0]);
   cudaFree(ctx->ws_far[1]);
   cudaFree(ctx->ws_far_stamp);
@@ -418,6 +422,7 @@ irgl_status irgl_debug_set(irgl_ctx* ctx, int key, int64_t value) {
     case 3: ctx->dbg_cap = value > 0 ? static_cast<uint32_t>(value) : 0; return IRGL_OK;
     case 4: ctx->dbg_big_cap = value > 0 ? static_cast<uint32_t>(value) : 0; return IRGL_OK;
     case 5: ctx->dbg_force_bottom_up = value > 0 ? 1u : 0u; return IRGL_OK;
+    case 6: ctx->dbg_held_lock = value >= 0 ? static_cast<uint32_t>(value) : 0xFFFFFFFFu; return IRGL_OK;
   }
   return fail(IRGL_ERR_INVALID_ARG, "unknown debug key %d", key);
 }

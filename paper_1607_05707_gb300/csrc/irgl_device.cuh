@@ -47,6 +47,8 @@ enum : uint32_t {
   DERR_BARRIER_TIMEOUT = 2,
   DERR_MAX_ROUNDS = 3,
   DERR_BAD_ITEM = 4,
+  DERR_LOCK_TIMEOUT = 5,   // an Atomic section's lock wait hit the time limit
+  DERR_MSF_ITERS = 6,      // more Boruvka iterations than a forest can need
 };
 
 // Device status block. Each contended family sits on its own 128-byte line.

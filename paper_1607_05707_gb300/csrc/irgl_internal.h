@@ -29,6 +29,9 @@ struct irgl_ctx {
   uint32_t ws_far_n = 0;
   uint32_t* ws_stamp = nullptr;  // SSSP/CC push dedup stamps
   uint32_t ws_stamp_n = 0;
+  uint32_t* msf_buf = nullptr;   // minimum spanning forest workspace (status block + 14 arrays of msf_n)
+  uint32_t msf_n = 0;
+  void* msf_host = nullptr;      // pinned copy of its status block
   uint32_t* ws_vis = nullptr;    // persistent BFS visited bitmap
   uint32_t ws_vis_words = 0;
   unsigned long long* ws_ds = nullptr;  // persistent SSSP packed (dist, round id) words
@@ -45,6 +48,7 @@ struct irgl_ctx {
   uint32_t dbg_cap = 0;
   uint32_t dbg_big_cap = 0;
   uint32_t dbg_force_bottom_up = 0;
+  uint32_t dbg_held_lock = 0xFFFFFFFFu;  // MSF: this component's lock starts held (never released)
 };
 
 struct irgl_graph {
@@ -85,6 +89,8 @@ irgl_status cuda_fail(cudaError_t e, const char* what);
 irgl_tuning default_tuning();
 irgl_status resolve_tuning(const irgl_tuning* in, irgl_tuning* out);
 irgl_status read_status(irgl_ctx* ctx, DevStatus* out);
+irgl_status status_from_device(const DevStatus& s);
+irgl_status control_cta(const uint32_t* masks, uint32_t count, uint32_t preferred, uint32_t* out);
 void reset_status(irgl_ctx* ctx);
 irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool need_far = false,
                              bool need_vis = false, bool need_ds = false);

@@ -26,12 +26,15 @@ IRGL_ERR_ADMISSION = -7
 IRGL_ERR_MAX_ROUNDS = -8
 IRGL_ERR_NOT_READY = -9
 IRGL_ERR_UNSUPPORTED = -10
+IRGL_ERR_LOCK_TIMEOUT = -11
 
 IRGL_INF = 0xFFFFFFFF
 
 IRGL_BFS, IRGL_SSSP, IRGL_CC, IRGL_CC_JUMP = 0, 1, 2, 3
 IRGL_PER_LAUNCH, IRGL_PERSISTENT = 0, 1
 IRGL_REDUCE_ANY, IRGL_REDUCE_ALL = 0, 1
+IRGL_LOCK_BLOCKING, IRGL_LOCK_TICKET, IRGL_LOCK_RETRY = 0, 1, 2
+LOCKS = {"blocking": IRGL_LOCK_BLOCKING, "ticket": IRGL_LOCK_TICKET, "retry": IRGL_LOCK_RETRY}
 
 IRGL_HOST_PTRS = 0x0
 IRGL_DEVICE_PTRS = 0x1
@@ -76,6 +79,27 @@ class irgl_stats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "device_ms"}
+        d["device_ms"] = float(self.device_ms)
+        return d
+
+
+class irgl_msf_stats(ctypes.Structure):
+    _fields_ = [
+        ("edges", c_uint32),
+        ("iterations", c_uint32),
+        ("weight", c_uint64),
+        ("invocations", c_uint32),
+        ("retries", c_uint32),
+        ("locks", c_uint32),
+        ("launches", c_uint32),
+        ("grid", c_uint32),
+        ("cta_size", c_uint32),
+        ("device_ms", ctypes.c_float),
+        ("reserved", c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k not in ("device_ms", "reserved")}
         d["device_ms"] = float(self.device_ms)
         return d
 
@@ -171,6 +195,7 @@ _SIGS = {
     "irgl_batch_info": [_P, POINTER(c_uint32), POINTER(c_uint32), POINTER(c_uint32), POINTER(c_int), POINTER(c_uint64)],
     "irgl_batch_result": [_P, c_uint32, POINTER(_P), POINTER(c_uint32), POINTER(c_uint32)],
     "irgl_batch_copy_result": [_P, c_uint32, _P],
+    "irgl_msf": [_P, _P, c_int, c_int, _P, c_uint32, c_int, POINTER(irgl_tuning), POINTER(irgl_msf_stats)],
 }
 _RESTYPE = {"irgl_last_error": c_char_p, "irgl_status_string": c_char_p}
 
@@ -484,3 +509,10 @@ def irgl_bfs_noalloc(device: int, cuda_stream: int | None, n: int, m: int, row_p
     rounds = c_uint32()
     _check(lib().irgl_bfs_noalloc(device, cuda_stream, n, m, row_ptr, col, src, level, ctypes.byref(rounds)))
     return int(rounds.value)
+
+
+def irgl_msf(ctx: int, g: int, mode: int, lock: int, out_edges: int, cap: int, out_on_host: int,
+             tuning=None) -> dict:
+    st = irgl_msf_stats()
+    _check(lib().irgl_msf(ctx, g, mode, lock, out_edges, cap, out_on_host, _tuning(tuning), ctypes.byref(st)))
+    return st.as_dict()
