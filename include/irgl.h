@@ -309,7 +309,10 @@ typedef struct {
   uint32_t max_slots;     /* concurrently active queries, 1..1024 */
   uint32_t epoch_rounds;  /* rounds per persistent launch */
   uint32_t count_edges;   /* 1: count out-edges of reached vertices per query (for GTEPS) */
-  uint32_t reserved;
+  uint32_t solo_min_n;    /* queries on graphs of at least this many vertices run alone, one
+                             persistent launch each between epochs, instead of sharing the batch
+                             arena (their state would evict the other queries' from L2); 0 = graphs
+                             whose state and stamps exceed half the L2, 0xFFFFFFFF = never */
   irgl_tuning tuning;     /* launch choices of the batched kernel (zeros = defaults) */
 } irgl_server_config;
 
@@ -329,6 +332,7 @@ typedef struct {
   uint32_t active, queued;
   uint64_t arena_entries;
   uint32_t grid, cta_size;
+  uint64_t solo;      /* completed queries that ran alone (solo_min_n) */
 } irgl_server_counters;
 
 irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irgl_server** out);

@@ -228,9 +228,10 @@ class Server:
     """Continuous-batching query server over device-resident graphs."""
 
     def __init__(self, ctx: Context, arena_bytes: int = 0, max_slots: int = 256, epoch_rounds: int = 64,
-                 count_edges: bool = True, tuning=None):
+                 count_edges: bool = True, tuning=None, solo_min_n: int = 0):
         self.ctx = ctx
-        self.handle = C.irgl_server_create(ctx.handle, arena_bytes, max_slots, epoch_rounds, int(count_edges), tuning)
+        self.handle = C.irgl_server_create(ctx.handle, arena_bytes, max_slots, epoch_rounds, int(count_edges), tuning,
+                                           solo_min_n)
         ctx._adopt(self)
 
     def submit(self, kernel: str, g: Graph, src: int, out: np.ndarray | None = None) -> int:

@@ -18,6 +18,13 @@
 //      slot are released.
 // The host/device boundary is crossed once per epoch and every device wait is
 // bounded, so no kernel spins indefinitely while the server idles.
+//
+// Queries on large graphs (solo_min_n vertices or more; by default those whose
+// state and stamps exceed half the L2) do not join the arena: between epochs
+// the worker runs one of them alone as a persistent single-query Iterate on a
+// private context bound to the server's stream. Such a query has enough
+// parallelism per round to fill the GPU, and alone its state stays in L2,
+// where in the arena every state access of every query would miss it.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -173,6 +180,13 @@ struct irgl_server {
   int32_t fatal = IRGL_OK;
   bool stop = false;
   std::thread worker;
+  // queries that run alone
+  uint32_t solo_min_n = 0xFFFFFFFFu;
+  irgl_ctx* solo_ctx = nullptr;
+  std::deque<Request> solo_q;
+  uint32_t* solo_state = nullptr;  // device result buffer (solo_cap entries)
+  uint64_t solo_cap = 0;
+  uint64_t solo_done = 0;
 };
 
 namespace {
@@ -202,7 +216,82 @@ void server_free(irgl_server* s) {
   if (s->h_scratch) cudaFreeHost(s->h_scratch);
   if (s->ev[0]) cudaEventDestroy(s->ev[0]);
   if (s->ev[1]) cudaEventDestroy(s->ev[1]);
+  cudaFree(s->solo_state);
+  if (s->solo_ctx) irgl_ctx_destroy(s->solo_ctx);
   if (s->stream) cudaStreamDestroy(s->stream);
+}
+
+// Ensure the pinned result sink holds n entries (worker thread only).
+cudaError_t ensure_scratch(irgl_server* s, uint64_t n) {
+  if (n <= s->scratch_n) return cudaSuccess;
+  if (s->h_scratch) cudaFreeHost(s->h_scratch);
+  s->h_scratch = nullptr;
+  s->scratch_n = 0;
+  cudaError_t e = cudaMallocHost(&s->h_scratch, sizeof(uint32_t) * n);
+  if (e == cudaSuccess) s->scratch_n = n;
+  return e;
+}
+
+// One query alone: persistent single-query Iterate on the private context,
+// then the reached-edge count and the result copy, all on the server's stream.
+void solo_step(irgl_server* s, const Request& rq) {
+  const double t0 = now_s();
+  const uint32_t n = rq.g->n;
+  cudaError_t e = cudaSuccess;
+  if (n > s->solo_cap) {
+    cudaFree(s->solo_state);
+    s->solo_state = nullptr;
+    s->solo_cap = 0;
+    e = cudaMalloc(&s->solo_state, sizeof(uint32_t) * std::max<uint32_t>(n, 4));
+    if (e == cudaSuccess) s->solo_cap = n;
+  }
+  uint32_t* dst = rq.host_out;
+  if (!dst && e == cudaSuccess) {
+    e = ensure_scratch(s, n);
+    dst = s->h_scratch;
+  }
+  irgl_stats st;
+  std::memset(&st, 0, sizeof(st));
+  irgl_status r = e == cudaSuccess ? IRGL_OK : IRGL_ERR_OOM;
+  float kms = 0.f;
+  if (r == IRGL_OK) {
+    cudaEventRecord(s->ev[0], s->stream);
+    const uint32_t src = rq.src;
+    r = irgl_run(s->solo_ctx, static_cast<irgl_kernel>(rq.op), rq.g, &src, 1, s->solo_state, 0, IRGL_PERSISTENT,
+                 nullptr, 0, &st);
+    cudaEventRecord(s->ev[1], s->stream);
+  }
+  if (r == IRGL_OK) {
+    e = cudaMemsetAsync(s->edge_cnt, 0, sizeof(unsigned long long), s->stream);
+    if (e == cudaSuccess && s->cfg.count_edges) {
+      k_reached_edges<<<static_cast<uint32_t>(s->ctx->sm_count), 256, 0, s->stream>>>(s->solo_state, rq.g->row_ptr, n,
+                                                                                     s->edge_cnt);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->h_edges, s->edge_cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst, s->solo_state, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) cudaEventElapsedTime(&kms, s->ev[0], s->ev[1]);
+    if (e != cudaSuccess) r = IRGL_ERR_CUDA;
+  }
+  const double t_done = now_s();
+  std::lock_guard<std::mutex> lk(s->mu);
+  Done d;
+  d.status = r;
+  d.rounds = st.rounds;
+  d.t_submit = rq.t_submit;
+  d.t_done = t_done;
+  d.edges = (r == IRGL_OK && s->cfg.count_edges) ? s->h_edges[0] : 0;
+  s->edges_total += d.edges;
+  s->rounds_total += st.rounds;
+  s->busy_s += t_done - t0;
+  s->kernel_s += kms * 1e-3;
+  s->done[rq.ticket] = d;
+  s->completed += 1;
+  s->solo_done += 1;
+  s->cv_done.notify_all();
 }
 
 // One scheduling step of the worker. Returns false when there was nothing to do.
@@ -211,10 +300,7 @@ bool server_step(irgl_server* s) {
   std::vector<Active> fresh;
   {
     std::unique_lock<std::mutex> lk(s->mu);
-    if (s->queue.empty() && s->active.empty()) {
-      s->cv.wait_for(lk, std::chrono::milliseconds(2));
-      if (s->queue.empty()) return false;
-    }
+    if (s->queue.empty() && s->active.empty()) return false;  // no batched work (the loop waits)
     while (!s->queue.empty() && !s->free_slots.empty()) {
       Request& rq = s->queue.front();
       uint64_t base = 0;
@@ -323,13 +409,7 @@ bool server_step(irgl_server* s) {
   uint64_t need = 0;
   for (auto& a : fin)
     if (!a.rq.host_out) need = std::max<uint64_t>(need, a.n);
-  if (need > s->scratch_n && e == cudaSuccess) {
-    if (s->h_scratch) cudaFreeHost(s->h_scratch);
-    s->h_scratch = nullptr;
-    s->scratch_n = 0;
-    e = cudaMallocHost(&s->h_scratch, sizeof(uint32_t) * need);
-    if (e == cudaSuccess) s->scratch_n = need;
-  }
+  if (e == cudaSuccess) e = ensure_scratch(s, need);
   for (auto& a : fin) {
     uint32_t* dst = a.rq.host_out ? a.rq.host_out : s->h_scratch;
     if (e == cudaSuccess)
@@ -375,11 +455,26 @@ bool server_step(irgl_server* s) {
 void server_loop(irgl_server* s) {
   DeviceGuard guard(s->ctx->device);
   for (;;) {
+    Request solo;
+    bool have_solo = false;
     {
-      std::lock_guard<std::mutex> lk(s->mu);
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->stop) break;
+      if (s->queue.empty() && s->active.empty() && s->solo_q.empty())
+        s->cv.wait_for(lk, std::chrono::milliseconds(2));
       if (s->stop) break;
     }
-    server_step(s);
+    server_step(s);  // one epoch of the batched queries, if any
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->fatal != IRGL_OK) break;
+      if (!s->solo_q.empty()) {
+        solo = s->solo_q.front();
+        s->solo_q.pop_front();
+        have_solo = true;
+      }
+    }
+    if (have_solo) solo_step(s, solo);  // then one large query alone
   }
 }
 
@@ -463,6 +558,22 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   s->grid = std::min<uint32_t>(s->grid, kMaxGrid);
   s->arena.init(s->arena_n);
   for (uint32_t i = 0; i < S; ++i) s->free_slots.push_back(S - 1 - i);
+  // queries that run alone: private context on the server's stream (used by the worker only)
+  if (cfg->solo_min_n == 0) {
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device);
+    s->solo_min_n = static_cast<uint32_t>(std::max<int64_t>(int64_t{l2} / 16, 1));  // 8 B of state + stamp per vertex > L2 / 2
+  } else {
+    s->solo_min_n = cfg->solo_min_n;
+  }
+  if (s->solo_min_n != 0xFFFFFFFFu) {
+    st = irgl_ctx_create(ctx->device, s->stream, &s->solo_ctx);
+    if (st != IRGL_OK) {
+      server_free(s);
+      delete s;
+      return st;
+    }
+  }
   s->worker = std::thread(server_loop, s);
   *out = s;
   return IRGL_OK;
@@ -478,7 +589,8 @@ irgl_status irgl_server_submit(irgl_server* s, irgl_graph* g, irgl_kernel k, uin
   if (g->ctx != s->ctx) return fail(IRGL_ERR_INVALID_ARG, "graph belongs to another context");
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->fatal != IRGL_OK) return fail(s->fatal, "server stopped after a device error");
-  if (static_cast<uint64_t>(g->n) > s->arena_n) {
+  const bool solo = g->n >= s->solo_min_n && s->solo_ctx != nullptr;
+  if (!solo && static_cast<uint64_t>(g->n) > s->arena_n) {
     s->rejected += 1;
     return fail(IRGL_ERR_ADMISSION, "query needs %u arena entries, the arena holds %llu", g->n,
                 (unsigned long long)s->arena_n);
@@ -490,7 +602,8 @@ irgl_status irgl_server_submit(irgl_server* s, irgl_graph* g, irgl_kernel k, uin
   rq.src = src;
   rq.host_out = host_out;
   rq.t_submit = now_s();
-  s->queue.push_back(rq);
+  if (solo) s->solo_q.push_back(rq);
+  else s->queue.push_back(rq);
   s->submitted += 1;
   *ticket = rq.ticket;
   s->cv.notify_one();
@@ -536,7 +649,8 @@ irgl_status irgl_server_stats(irgl_server* s, irgl_server_counters* out) {
   out->busy_s = s->busy_s;
   out->kernel_s = s->kernel_s;
   out->active = static_cast<uint32_t>(s->active.size());
-  out->queued = static_cast<uint32_t>(s->queue.size());
+  out->queued = static_cast<uint32_t>(s->queue.size() + s->solo_q.size());
+  out->solo = s->solo_done;
   out->arena_entries = s->arena_n;
   out->grid = s->grid;
   out->cta_size = s->t.cta_size;

@@ -110,7 +110,7 @@ class irgl_server_config(ctypes.Structure):
         ("max_slots", c_uint32),
         ("epoch_rounds", c_uint32),
         ("count_edges", c_uint32),
-        ("reserved", c_uint32),
+        ("solo_min_n", c_uint32),
         ("tuning", irgl_tuning),
     ]
 
@@ -132,6 +132,7 @@ class irgl_server_counters(ctypes.Structure):
         ("rounds", c_uint64), ("edges", c_uint64), ("busy_s", ctypes.c_double), ("kernel_s", ctypes.c_double),
         ("active", c_uint32),
         ("queued", c_uint32), ("arena_entries", c_uint64), ("grid", c_uint32), ("cta_size", c_uint32),
+        ("solo", c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -446,12 +447,13 @@ def irgl_trace_read(ctx: int, cap: int = 1 << 16):
 
 
 def irgl_server_create(ctx: int, arena_bytes: int = 0, max_slots: int = 256, epoch_rounds: int = 64,
-                       count_edges: int = 1, tuning=None) -> int:
+                       count_edges: int = 1, tuning=None, solo_min_n: int = 0) -> int:
     cfg = irgl_server_config()
     cfg.arena_bytes = arena_bytes
     cfg.max_slots = max_slots
     cfg.epoch_rounds = epoch_rounds
     cfg.count_edges = count_edges
+    cfg.solo_min_n = solo_min_n
     if tuning is not None:
         for k, v in dict(tuning).items():
             setattr(cfg.tuning, k, int(v))

@@ -129,3 +129,22 @@ def test_server_arrivals_while_running(env):
     st = srv.stats()
     assert st["rounds"] < sum(i["rounds"] for i in infos)
     srv.close()
+
+
+def test_server_large_queries_run_alone(env):
+    """Graphs of solo_min_n vertices or more skip the arena: their queries run alone
+    between epochs, mixed with batched ones; every result is still the oracle's."""
+    from paper_1607_05707_gb300.api import Server
+
+    ctx, graphs, dgs = env
+    qs = _queries(graphs, 40, seed=12)
+    srv = Server(ctx, arena_bytes=64 << 20, max_slots=16, epoch_rounds=8, solo_min_n=16384)
+    bufs = [np.empty(graphs[gi].n, dtype=np.uint32) for _, gi, _ in qs]
+    tickets = [srv.submit(k, dgs[gi], s, b) for (k, gi, s), b in zip(qs, bufs)]
+    srv.drain(120)
+    for q, b, t in zip(qs, bufs, tickets):
+        _check(graphs, q, b, srv.poll(t))
+    st = srv.stats()
+    n_solo = sum(1 for _, gi, _ in qs if graphs[gi].n >= 16384)
+    assert st["completed"] == len(qs) and st["solo"] == n_solo and 0 < n_solo < len(qs)
+    srv.close()
