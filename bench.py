@@ -28,6 +28,7 @@ import platform
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 from pathlib import Path
 
@@ -67,6 +68,8 @@ def parse_args():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--clocks-log", type=str, default=os.environ.get("IRGL_CLOCKS_LOG"),
+                    help="directory that keeps the raw nvidia-smi clock samples (default: a temporary file)")
     ap.add_argument("--no-per-launch", action="store_true", help="skip the per-launch (host loop) BFS comparison")
     ap.add_argument("--tuning", type=str, default="", help="JSON irgl_tuning overrides")
     ap.add_argument("--trace", action="store_true", help="print a per-round trace of one query per kernel to stderr")
@@ -130,15 +133,21 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    # directory for the raw samples (kept for evidence); a temporary file when unset
+    LOG_DIR: str | None = None
+
     def __init__(self, device_index: int, enabled: bool = True):
         self.proc = None
         self.path = None
         self.device_index = device_index
         if not enabled:
             return
-        out = ROOT / "gpurun_out"
-        out.mkdir(exist_ok=True)
-        self.path = out / f"clocks_{os.getpid()}.csv"
+        if self.LOG_DIR:
+            out = Path(self.LOG_DIR)
+            out.mkdir(parents=True, exist_ok=True)
+            self.path = out / f"clocks_{os.getpid()}.csv"
+        else:
+            self.path = Path(tempfile.gettempdir()) / f"irgl_clocks_{os.getpid()}.csv"
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={device_index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
@@ -856,6 +865,7 @@ def run_msf(args, world, rank, local):
 
 def main():
     args = parse_args()
+    ClockSampler.LOG_DIR = args.clocks_log
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_init(args)

@@ -104,10 +104,10 @@ typedef struct {
                                  through L1, filters edges to visited vertices before the level is
                                  read from L2 (off by default: slower on R-MAT scale 20, where the
                                  bit updates cost more than the L2 reads they save) */
-#define IRGL_TUNE_NO_PACKED 0x8u /* persistent SSSP without near-far: keep distances and the
-                                    dedup stamps in two arrays (by default one 64-bit word per
-                                    vertex holds both, lowered by one atomicMin, and the distances
-                                    are copied to the output at the end) */
+#define IRGL_TUNE_NO_PACKED 0x8u /* persistent SSSP: keep distances and the dedup stamps in two
+                                    arrays (by default one 64-bit word per vertex holds both,
+                                    lowered by one atomicMin, and the distances are copied to the
+                                    output at the end) */
 
 /* Per-call counters. */
 typedef struct {

@@ -758,7 +758,7 @@ irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workl
   if (s != IRGL_OK) return s;
   DeviceGuard guard(ctx->device);
   const bool vis = k == IRGL_BFS && mode == IRGL_PERSISTENT && (t.flags & IRGL_TUNE_BITMAP);
-  const bool packed = k == IRGL_SSSP && mode == IRGL_PERSISTENT && t.delta == 0 && !(t.flags & IRGL_TUNE_NO_PACKED);
+  const bool packed = k == IRGL_SSSP && mode == IRGL_PERSISTENT && !(t.flags & IRGL_TUNE_NO_PACKED);
   const bool far = (k == IRGL_SSSP || k == IRGL_CC) && mode == IRGL_PERSISTENT && t.delta != 0;
   s = ensure_workspace(ctx, g->n, k != IRGL_BFS, far, vis, packed);
   if (s != IRGL_OK) return s;

@@ -623,11 +623,17 @@ __device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state
   }
   if (OP == OP_SSSP && rc.ds != nullptr) {
     // one 64-bit atomicMin lowers the distance and stamps the round: v is
-    // pushed by the thread that lowers it first in this round
+    // pushed by the thread that lowers it first in this round (a far
+    // improvement stamps 0: see decide_n)
     const uint32_t nd = val + static_cast<uint32_t>(wt);
     if (nd >= cur) return 0u;
-    const unsigned long long old = atomicMin(rc.ds + v, (static_cast<unsigned long long>(nd) << 32) | rc.dsr);
-    return (nd < static_cast<uint32_t>(old >> 32) && static_cast<uint32_t>(old) != rc.dsr) ? 1u : 0u;
+    const bool far = rc.limit != kInf && nd >= rc.limit;
+    const unsigned long long old =
+        atomicMin(rc.ds + v, (static_cast<unsigned long long>(nd) << 32) | (far ? 0u : rc.dsr));
+    if (nd >= static_cast<uint32_t>(old >> 32)) return 0u;
+    if (!far) return static_cast<uint32_t>(old) != rc.dsr ? 1u : 0u;
+    nd_out = nd;
+    return atomicExch(rc.far_stamp + v, rc.phase) != rc.phase ? 2u : 0u;
   }
   if (!kNearFarOp<OP> || rc.limit == kInf) return decide<OP>(op_rt, state, stamp, v, val, wt, cur, rc.ep) ? 1u : 0u;
   const uint32_t nd = OP == OP_SSSP ? val + static_cast<uint32_t>(wt) : val;
@@ -642,14 +648,15 @@ __device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state
 // The operator on N edges of one lane at once. Every atomic whose result
 // decides a push is issued before any of those results is read, so the N L2
 // round trips overlap instead of following one another. Same outcome as
-// decide_route edge by edge (which near-far rounds and pointer-jumping CC keep
-// using). `state`/`stamp` are array bases, edge k's vertex is sb[k] + v[k].
+// decide_route edge by edge (which pointer-jumping CC keeps using), near-far
+// routing included. `state`/`stamp` are array bases, edge k's vertex is
+// sb[k] + v[k].
 template <uint32_t OP, int N>
 __device__ __forceinline__ void decide_n(const RoundCtx& rc, uint32_t* state, uint32_t* stamp,
                                          const uint32_t (&op)[N], const uint32_t (&sb)[N], const uint32_t (&v)[N],
                                          const uint32_t (&val)[N], const int32_t (&wt)[N], const uint32_t (&cur)[N],
                                          uint32_t valid, uint32_t (&r)[N], uint32_t (&nd)[N]) {
-  if (OP == OP_CCJ || (kNearFarOp<OP> && rc.limit != kInf)) {
+  if (OP == OP_CCJ) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       nd[k] = 0;
@@ -666,7 +673,13 @@ __device__ __forceinline__ void decide_n(const RoundCtx& rc, uint32_t* state, ui
     nd[k] = o == OP_SSSP ? val[k] + static_cast<uint32_t>(wt[k]) : val[k];
     t[k] = ((valid >> k) & 1u) != 0 && (o == OP_BFS ? cur[k] == kInf : nd[k] < cur[k]);
   }
-  if (OP == OP_SSSP && rc.ds != nullptr) {
+  // near-far: an improvement to a value >= the limit goes to the far list,
+  // deduplicated per phase by far_stamp (route 2)
+  const bool nf = kNearFarOp<OP> && rc.limit != kInf;
+  bool far[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) far[k] = nf && nd[k] >= rc.limit;
+  if (OP == OP_SSSP && rc.ds != nullptr && !nf) {
     unsigned long long old[N];
 #pragma unroll
     for (int k = 0; k < N; ++k)
@@ -674,6 +687,29 @@ __device__ __forceinline__ void decide_n(const RoundCtx& rc, uint32_t* state, ui
 #pragma unroll
     for (int k = 0; k < N; ++k)
       r[k] = (t[k] && nd[k] < static_cast<uint32_t>(old[k] >> 32) && static_cast<uint32_t>(old[k]) != rc.dsr) ? 1u : 0u;
+    return;
+  }
+  if (OP == OP_SSSP && rc.ds != nullptr) {
+    // A far improvement writes round id 0: the vertex is not on this round's
+    // out-worklist (its value was >= the limit, so no near push happened this
+    // round), and a later near improvement in the round must still push it.
+    unsigned long long old[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      old[k] = t[k] ? atomicMin(rc.ds + v[k], (static_cast<unsigned long long>(nd[k]) << 32) | (far[k] ? 0u : rc.dsr))
+                    : 0ull;
+    bool imp[N];
+    uint32_t fx[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      imp[k] = t[k] && nd[k] < static_cast<uint32_t>(old[k] >> 32);
+      fx[k] = ~rc.phase;
+      if (imp[k] && far[k]) fx[k] = atomicExch(rc.far_stamp + v[k], rc.phase);
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      r[k] = !imp[k] ? 0u
+                     : far[k] ? (fx[k] != rc.phase ? 2u : 0u) : (static_cast<uint32_t>(old[k]) != rc.dsr ? 1u : 0u);
     return;
   }
   uint32_t old[N];
@@ -690,13 +726,14 @@ __device__ __forceinline__ void decide_n(const RoundCtx& rc, uint32_t* state, ui
   for (int k = 0; k < N; ++k) {
     const uint32_t o = OP == OP_RUNTIME ? op[k] : OP;
     imp[k] = t[k] && (o == OP_BFS ? old[k] == kInf : nd[k] < old[k]);
-    ex[k] = ~rc.ep;
-    if (imp[k] && o != OP_BFS) ex[k] = atomicExch(stamp + sb[k] + v[k], rc.ep);
+    ex[k] = far[k] ? ~rc.phase : ~rc.ep;
+    if (imp[k] && o != OP_BFS)
+      ex[k] = far[k] ? atomicExch(rc.far_stamp + sb[k] + v[k], rc.phase) : atomicExch(stamp + sb[k] + v[k], rc.ep);
   }
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const uint32_t o = OP == OP_RUNTIME ? op[k] : OP;
-    r[k] = (imp[k] && (o == OP_BFS || ex[k] != rc.ep)) ? 1u : 0u;
+    r[k] = (imp[k] && (o == OP_BFS || ex[k] != (far[k] ? rc.phase : rc.ep))) ? (far[k] ? 2u : 1u) : 0u;
     if (OP == OP_BFS && r[k] != 0u) {
       if (rc.vis) atomicOr(rc.vis + (v[k] >> 5), 1u << (v[k] & 31u));
       if (rc.mf)
@@ -1283,9 +1320,12 @@ __device__ __forceinline__ void split_far(const V& g, Smem<CTA>& sm, const Round
     uint32_t v = 0, d = kInf;
     if (i < far_n) {
       v = __ldcg(fin + i);
-      d = __ldcg(g.state + v);
+      d = (OP == OP_SSSP && rc.ds != nullptr) ? static_cast<uint32_t>(__ldcg(rc.ds + v) >> 32) : __ldcg(g.state + v);
     }
-    const bool near = i < far_n && d >= lim_old && d < lim_new && atomicExch(g.stamp + v, rc.ep) != rc.ep;
+    // each vertex is on a phase's far list at most once and a split round
+    // relaxes nothing, so with the packed words no round stamp is needed here
+    const bool near = i < far_n && d >= lim_old && d < lim_new &&
+                      ((OP == OP_SSSP && rc.ds != nullptr) || atomicExch(g.stamp + v, rc.ep) != rc.ep);
     const bool keep = i < far_n && d >= lim_new && atomicExch(rc.far_stamp + v, rc.phase) != rc.phase;
     push1<CTA>(sm, rc.out, near, v);
     push_far4<CTA>(sm, rc.far_out, keep ? 1u : 0u, v, 0u, 0u, 0u, d);
