@@ -265,7 +265,8 @@ irgl_status irgl_autotune(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uin
  * shared double-buffered worklist as arena offsets that a sorted offset table
  * maps back to the instance, and its termination flag is the round of its
  * last push. Instances may differ in graph, size and kernel; the CTA size is
- * chosen by the T_control rule above. irgl_batch_prepare allocates the arena
+ * chosen by the T_control rule above, with the tuning's CTA size (default 128)
+ * as the preference. irgl_batch_prepare allocates the arena
  * (16 bytes per instance vertex), uploads the descriptors and, with
  * use_cuda_graph = 1, captures the whole launch sequence (admission kernels +
  * persistent kernel) in a CUDA graph that irgl_batch_launch replays (if the
