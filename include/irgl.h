@@ -266,10 +266,13 @@ irgl_status irgl_autotune(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uin
  * maps back to the instance, and its termination flag is the round of its
  * last push. Instances may differ in graph, size and kernel; the CTA size is
  * chosen by the T_control rule above, with the tuning's CTA size (default 128)
- * as the preference. irgl_batch_prepare allocates the arena
- * (16 bytes per instance vertex), uploads the descriptors and, with
- * use_cuda_graph = 1, captures the whole launch sequence (admission kernels +
- * persistent kernel) in a CUDA graph that irgl_batch_launch replays (if the
+ * as the preference. irgl_batch_prepare allocates the arena (20 bytes per
+ * instance vertex: a 64-bit word holding the value and the id of the round
+ * that last lowered it, the u32 result and two worklist entries; 16 bytes with
+ * IRGL_TUNE_NO_PACKED, which keeps values and stamps in two arrays), uploads
+ * the descriptors and, with use_cuda_graph = 1, captures the whole launch
+ * sequence (admission kernels + persistent kernel + result extraction) in a
+ * CUDA graph that irgl_batch_launch replays (if the
  * capture fails the sequence is launched directly; irgl_batch_info tells).
  * Every launch recomputes all instances from their sources.
  * Queries are added before prepare; query ids are 0, 1, ... in add order. */
@@ -298,8 +301,9 @@ irgl_status irgl_batch_autotune(irgl_batch* b, uint32_t reps, irgl_tuning* best,
 /* ---------------------------------------------------------------- serving
  * Continuous batching server for BFS/SSSP queries against device-resident
  * graphs. A worker thread admits queued queries in arrival order while a
- * slot is free and the query's state fits the device arena (16 bytes per
- * vertex of its graph; first-fit), launches epochs of the batched persistent
+ * slot is free and the query's state fits the device arena (20 bytes per
+ * vertex of its graph, 16 with IRGL_TUNE_NO_PACKED; first-fit), launches
+ * epochs of the batched persistent
  * kernel (at most epoch_rounds rounds over every active query), and retires
  * the queries that finished: their result is copied to the caller's host
  * buffer (if one was given), and their memory and slot are reused. Queries

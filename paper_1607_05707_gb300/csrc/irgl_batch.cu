@@ -1,8 +1,11 @@
 // Batching: many independent queries (instances) in one persistent cooperative
 // launch, captured once in a CUDA graph and replayed.
 //
-// Layout: instance q owns arena[base_q, base_q + n_q) of the state arena and the
-// same range of the stamp arena; its worklist items are arena indices on the
+// Layout: instance q owns arena[base_q, base_q + n_q) of the packed arena (one
+// 64-bit word per vertex: value and the id of the round that last lowered it;
+// with IRGL_TUNE_NO_PACKED a state and a stamp arena instead) and the same
+// range of the u32 result arena, filled from the packed words after each run;
+// its worklist items are arena indices on the
 // shared double-buffered worklist; its termination flag is qlast[q], the round
 // of its last push. Bases are assigned in insertion order, so the descriptor
 // table is sorted by base and an item maps back to its instance by binary
@@ -42,7 +45,8 @@ struct irgl_batch {
   DevStatus* st = nullptr;
   DevStatus* st_host = nullptr;
   uint32_t* state = nullptr;
-  uint32_t* stamp = nullptr;
+  uint32_t* stamp = nullptr;          // two-array form only (IRGL_TUNE_NO_PACKED)
+  unsigned long long* ds = nullptr;   // packed (value, round id) arena
   uint32_t* items[2] = {nullptr, nullptr};
   uint32_t* qlast = nullptr;
   uint32_t* qlast_host = nullptr;
@@ -107,6 +111,7 @@ void batch_free_device(irgl_batch* b) {
   b->graph = nullptr;
   cudaFree(b->state);
   cudaFree(b->stamp);
+  cudaFree(b->ds);
   cudaFree(b->items[0]);
   cudaFree(b->items[1]);
   cudaFree(b->qlast);
@@ -122,6 +127,7 @@ void batch_free_device(irgl_batch* b) {
   b->big_cap = 0;
   if (b->qlast_host) cudaFreeHost(b->qlast_host);
   b->state = b->stamp = b->items[0] = b->items[1] = b->qlast = b->cont = b->srcs = b->sbases = nullptr;
+  b->ds = nullptr;
   b->qlast_host = nullptr;
   b->desc = nullptr;
   b->qnew = nullptr;
@@ -142,6 +148,8 @@ cudaError_t enqueue(irgl_batch* b) {
   cudaError_t e = cudaMemsetAsync(b->cont, 0, 2 * sizeof(uint32_t), b->stream);
   if (e == cudaSuccess) e = launch_admit(b->ap, b->admit_grid, b->stream);
   if (e == cudaSuccess) e = launch_batch_iterate(b->t.cta_size, b->grid, b->bp, b->stream);
+  // results: the value halves of the packed words
+  if (e == cudaSuccess && b->ds) e = launch_extract_values(b->ds, b->state, b->arena_n, b->admit_grid, b->stream);
   return e;
 }
 
@@ -262,8 +270,14 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
                  q.base, 0};
     flat.insert(flat.end(), q.srcs.begin(), q.srcs.end());
   }
+  // packed (value, round id) words unless the two-array form is asked for; the
+  // u32 state arena then holds the results, extracted after each run
+  const bool packed = !(t.flags & IRGL_TUNE_NO_PACKED);
   cudaError_t e = cudaMalloc(&b->state, sizeof(uint32_t) * b->arena_n);
-  if (e == cudaSuccess) e = cudaMalloc(&b->stamp, sizeof(uint32_t) * b->arena_n);
+  if (e == cudaSuccess) {
+    if (packed) e = cudaMalloc(&b->ds, sizeof(unsigned long long) * b->arena_n);
+    else e = cudaMalloc(&b->stamp, sizeof(uint32_t) * b->arena_n);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&b->items[0], sizeof(uint32_t) * b->arena_n);
   if (e == cudaSuccess) e = cudaMalloc(&b->items[1], sizeof(uint32_t) * b->arena_n);
   if (e == cudaSuccess) e = cudaMalloc(&b->qlast, sizeof(uint32_t) * Q);
@@ -281,7 +295,7 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
     batch_free_device(b);
     return cuda_fail(e, "batch arena allocation");
   }
-  e = cudaMemsetAsync(b->stamp, 0, sizeof(uint32_t) * b->arena_n, b->stream);
+  if (b->stamp) e = cudaMemsetAsync(b->stamp, 0, sizeof(uint32_t) * b->arena_n, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->cont, 0, 128, b->stream);
   if (e == cudaSuccess && !flat.empty())
     e = cudaMemcpyAsync(b->srcs, flat.data(), sizeof(uint32_t) * flat.size(), cudaMemcpyHostToDevice, b->stream);
@@ -312,6 +326,7 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   b->bp.nq = Q;
   b->bp.state = b->state;
   b->bp.stamp = b->stamp;
+  b->bp.ds = b->ds;
   b->bp.qlast = b->qlast;
   b->bp.items[0] = b->items[0];
   b->bp.items[1] = b->items[1];
@@ -331,6 +346,7 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   b->ap.total = static_cast<uint32_t>(total);
   b->ap.srcs = b->srcs;
   b->ap.state = b->state;
+  b->ap.ds = b->ds;
   b->ap.qlast = b->qlast;
   b->ap.items[0] = b->items[0];
   b->ap.items[1] = b->items[1];

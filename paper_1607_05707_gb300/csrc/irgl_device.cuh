@@ -39,6 +39,11 @@ enum : uint32_t { OP_BFS = 0, OP_SSSP = 1, OP_CC = 2, OP_RUNTIME = 3, OP_CCJ = 4
 // distances and min-label CC labels.
 template <uint32_t OP>
 constexpr bool kNearFarOp = OP == OP_SSSP || OP == OP_CC;
+
+// Operators that can keep (value, round id) in one 64-bit word per vertex:
+// single-graph SSSP, and every query of the batched kernel.
+template <uint32_t OP>
+constexpr bool kPackedOp = OP == OP_SSSP || OP == OP_RUNTIME;
 enum : int { RED_NONE = 0, RED_ANY = 1, RED_ALL = 2 };
 // Device error codes (first one wins).
 enum : uint32_t {
@@ -194,8 +199,9 @@ struct BParams {
   const QDesc* desc;        // nq descriptors, sorted by base
   const uint32_t* sbases;   // nq sorted bases
   uint32_t nq;
-  uint32_t* state;          // arena: state of every query
-  uint32_t* stamp;          // arena: push dedup stamps
+  uint32_t* state;          // arena: result of every query (filled from ds after the run)
+  uint32_t* stamp;          // arena: push dedup stamps (unused when ds is set)
+  unsigned long long* ds;   // arena: (value << 32) | id of the round that last lowered it
   uint32_t* qlast;          // per query id: stamp (round id) of its last push
   uint32_t* items[2];       // shared worklists of arena indices
   uint32_t cap;
@@ -594,9 +600,9 @@ struct RoundCtx {
 // stale clear bit (set later in this round, or cached before) falls through
 // to the L2 read of the level, which decides.
 template <uint32_t OP>
-__device__ __forceinline__ uint32_t load_cur(const RoundCtx& rc, const uint32_t* state, uint32_t v) {
+__device__ __forceinline__ uint32_t load_cur(const RoundCtx& rc, const uint32_t* state, uint32_t sb, uint32_t v) {
   if (OP == OP_BFS && rc.vis != nullptr && ((rc.vis[v >> 5] >> (v & 31u)) & 1u)) return 0u;
-  if (OP == OP_SSSP && rc.ds != nullptr) return static_cast<uint32_t>(__ldcg(rc.ds + v) >> 32);
+  if (kPackedOp<OP> && rc.ds != nullptr) return static_cast<uint32_t>(__ldcg(rc.ds + sb + v) >> 32);
   return __ldcg(state + v);
 }
 
@@ -621,15 +627,16 @@ __device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state
     if (p && rc.mf) atomicAdd(rc.mf, static_cast<unsigned long long>(__ldg(rc.row_ptr + v + 1) - __ldg(rc.row_ptr + v)));
     return p ? 1u : 0u;
   }
-  if (OP == OP_SSSP && rc.ds != nullptr) {
-    // one 64-bit atomicMin lowers the distance and stamps the round: v is
+  if (kPackedOp<OP> && rc.ds != nullptr) {
+    // one 64-bit atomicMin lowers the value and stamps the round: v is
     // pushed by the thread that lowers it first in this round (a far
-    // improvement stamps 0: see decide_n)
-    const uint32_t nd = val + static_cast<uint32_t>(wt);
-    if (nd >= cur) return 0u;
-    const bool far = rc.limit != kInf && nd >= rc.limit;
+    // improvement stamps 0: see decide_n). BFS levels are lowered from INF.
+    const uint32_t o = OP == OP_RUNTIME ? op_rt : OP;
+    const uint32_t nd = o == OP_SSSP ? val + static_cast<uint32_t>(wt) : val;
+    if (o == OP_BFS ? cur != kInf : nd >= cur) return 0u;
+    const bool far = OP == OP_SSSP && rc.limit != kInf && nd >= rc.limit;
     const unsigned long long old =
-        atomicMin(rc.ds + v, (static_cast<unsigned long long>(nd) << 32) | (far ? 0u : rc.dsr));
+        atomicMin(rc.ds + sb + v, (static_cast<unsigned long long>(nd) << 32) | (far ? 0u : rc.dsr));
     if (nd >= static_cast<uint32_t>(old >> 32)) return 0u;
     if (!far) return static_cast<uint32_t>(old) != rc.dsr ? 1u : 0u;
     nd_out = nd;
@@ -679,11 +686,11 @@ __device__ __forceinline__ void decide_n(const RoundCtx& rc, uint32_t* state, ui
   bool far[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) far[k] = nf && nd[k] >= rc.limit;
-  if (OP == OP_SSSP && rc.ds != nullptr && !nf) {
+  if (kPackedOp<OP> && rc.ds != nullptr && !nf) {
     unsigned long long old[N];
 #pragma unroll
     for (int k = 0; k < N; ++k)
-      old[k] = t[k] ? atomicMin(rc.ds + v[k], (static_cast<unsigned long long>(nd[k]) << 32) | rc.dsr) : 0ull;
+      old[k] = t[k] ? atomicMin(rc.ds + sb[k] + v[k], (static_cast<unsigned long long>(nd[k]) << 32) | rc.dsr) : 0ull;
 #pragma unroll
     for (int k = 0; k < N; ++k)
       r[k] = (t[k] && nd[k] < static_cast<uint32_t>(old[k] >> 32) && static_cast<uint32_t>(old[k]) != rc.dsr) ? 1u : 0u;
@@ -791,7 +798,7 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
     if (e < lim) {
       v = ld_adj(col + e);
       const int32_t wt = nw ? ld_adj(w + e) : 0;
-      r = decide_route<OP>(op, state, stamp, v, val, wt, load_cur<OP>(rc, state, v), rc, sb, nd);
+      r = decide_route<OP>(op, state, stamp, v, val, wt, load_cur<OP>(rc, state, sb, v), rc, sb, nd);
     }
     push1<CTA>(sm, rc.out, r == 1u, sb + v);
     if (kNearFarOp<OP>) push_far4<CTA>(sm, rc.far_out, r == 2u ? 1u : 0u, sb + v, 0u, 0u, 0u, nd);
@@ -814,7 +821,7 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
       const uint32_t vals[4] = {val, val, val, val};
       uint32_t cc[4], rr[4], ndv[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) cc[k] = load_cur<OP>(rc, state, vv[k]);
+      for (int k = 0; k < 4; ++k) cc[k] = load_cur<OP>(rc, state, sb, vv[k]);
       decide_n<OP, 4>(rc, state, stamp, ops, zero, vv, vals, wv, cc, 0xFu, rr, ndv);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -859,8 +866,11 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
       beg = __ldg(rp + u);
       end = __ldg(rp + u + 1);
       const uint32_t op = g.op(q);
-      if (op == OP_BFS) val = V::kBatched ? __ldcg(g.state + item) + 1u : rc.bfs_val;
-      else if (OP == OP_SSSP && rc.ds != nullptr) val = static_cast<uint32_t>(__ldcg(rc.ds + item) >> 32);
+      if (kPackedOp<OP> && rc.ds != nullptr && (OP != OP_RUNTIME || op != OP_BFS))
+        val = static_cast<uint32_t>(__ldcg(rc.ds + item) >> 32);
+      else if (op == OP_BFS)
+        val = !V::kBatched ? rc.bfs_val
+                           : (rc.ds != nullptr ? static_cast<uint32_t>(__ldcg(rc.ds + item) >> 32) : __ldcg(g.state + item)) + 1u;
       else val = __ldcg(g.state + item);
     }
   }
@@ -974,7 +984,7 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
     }
 #pragma unroll
     for (uint32_t k = 0; k < E; ++k)
-      cur[k] = (base + k * 32 + lane < total) ? load_cur<OP>(rc, g.state + sb[k], v[k]) : 0u;
+      cur[k] = (base + k * 32 + lane < total) ? load_cur<OP>(rc, g.state + sb[k], sb[k], v[k]) : 0u;
     uint32_t f = 0, ff = 0, dmin = kInf, vmask = 0, rr[E], ndv[E];
 #pragma unroll
     for (uint32_t k = 0; k < E; ++k) vmask |= (base + k * 32 + lane < total ? 1u : 0u) << k;
@@ -1222,7 +1232,7 @@ __device__ __forceinline__ void big_phase(const V& g, Smem<CTA>& sm, const Round
         }
 #pragma unroll
         for (uint32_t k = 0; k < E; ++k)
-          cur[k] = (base + k * 32 + lane < wend) ? load_cur<OP>(rc, g.state + sb[k], v[k]) : 0u;
+          cur[k] = (base + k * 32 + lane < wend) ? load_cur<OP>(rc, g.state + sb[k], sb[k], v[k]) : 0u;
         uint32_t f = 0, ff = 0, dmin = kInf, vmask = 0, rr[E], ndv[E];
 #pragma unroll
         for (uint32_t k = 0; k < E; ++k) vmask |= (base + k * 32 + lane < wend ? 1u : 0u) << k;
@@ -1822,8 +1832,8 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
     rc.mf = nullptr;
     rc.row_ptr = nullptr;
     rc.vis = nullptr;
-    rc.ds = nullptr;
-    rc.dsr = 0;
+    rc.ds = p.ds;     // round ids are the global ones: admission writes id 0
+    rc.dsr = rc.ep;
     if (threadIdx.x == 0) {
       if (blockIdx.x == 0) {
         st->tail[(r + 2) % 3] = 0;
@@ -1878,6 +1888,7 @@ struct AdmitParams {
   uint32_t total;         // sum of n over the new queries
   const uint32_t* srcs;   // flat sources (vertex ids local to each query's graph)
   uint32_t* state;
+  unsigned long long* ds; // packed arena (when set, the initial values go here)
   uint32_t* qlast;
   uint32_t* items[2];
   uint32_t cap;
@@ -1925,7 +1936,9 @@ __device__ __forceinline__ void admit_fill(const AdmitParams& a) {
       const QNew q = a.qn[j];
       const uint32_t v = i - q.pre;
       item = q.base + v;
-      __stcg(a.state + item, q.op == OP_CC ? v : kInf);
+      const uint32_t init = q.op == OP_CC ? v : kInf;
+      if (a.ds != nullptr) __stcg(a.ds + item, static_cast<unsigned long long>(init) << 32);
+      else __stcg(a.state + item, init);
       push = q.op == OP_CC;
     }
     append_pending(a, buf, push, item);
@@ -1952,7 +1965,7 @@ __device__ __forceinline__ void admit_sources(const AdmitParams& a) {
         if (v < q.n) {
           item = q.base + v;
           // a repeated source is pushed once
-          p = atomicExch(a.state + item, 0u) != 0u;
+          p = a.ds != nullptr ? (atomicExch(a.ds + item, 0ull) >> 32) != 0u : atomicExch(a.state + item, 0u) != 0u;
         }
       }
       append_pending(a, buf, p, item);

@@ -13,6 +13,15 @@ __global__ void __launch_bounds__(CTA, MinBlocks<CTA>::value) k_batch_iterate(BP
 __global__ void __launch_bounds__(256) k_batch_fill(AdmitParams a) { admit_fill(a); }
 __global__ void __launch_bounds__(256) k_batch_sources(AdmitParams a) { admit_sources(a); }
 
+// Results out of the packed arena: out[i] = ds[i] >> 32 (the value half),
+// two entries per thread per step.
+__global__ void __launch_bounds__(256) k_extract_values(const unsigned long long* __restrict__ ds,
+                                                        uint32_t* __restrict__ out, uint64_t n) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    __stcs(out + i, static_cast<uint32_t>(__ldcs(ds + i) >> 32));
+}
+
 namespace {
 
 template <int CTA>
@@ -50,6 +59,13 @@ cudaError_t occupancy_batch(uint32_t cta, int* nb) {
     case 1024: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_batch_iterate<1024>, 1024, 0);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_extract_values(const unsigned long long* ds, uint32_t* out, uint64_t n, uint32_t grid,
+                                  cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_extract_values<<<grid, 256, 0, s>>>(ds, out, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_admit(const AdmitParams& a, uint32_t grid, cudaStream_t s) {

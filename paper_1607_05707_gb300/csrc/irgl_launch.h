@@ -27,6 +27,9 @@ cudaError_t launch_wl_append(uint32_t* items, uint32_t* tail, uint32_t cap, cons
 cudaError_t launch_batch_iterate(uint32_t cta, uint32_t grid, const BParams& p, cudaStream_t s);
 cudaError_t occupancy_batch(uint32_t cta, int* blocks_per_sm);
 cudaError_t launch_admit(const AdmitParams& a, uint32_t grid, cudaStream_t s);
+// out[i] = value half of the packed arena word ds[i], i < n.
+cudaError_t launch_extract_values(const unsigned long long* ds, uint32_t* out, uint64_t n, uint32_t grid,
+                                  cudaStream_t s);
 
 inline bool valid_cta(uint32_t cta) { return cta == 128 || cta == 256 || cta == 512 || cta == 1024; }
 

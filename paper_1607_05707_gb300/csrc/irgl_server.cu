@@ -3,9 +3,10 @@
 //
 // A host worker thread repeats:
 //   1. admission: take queued queries in arrival order while a slot is free and
-//      the query's state (16 bytes per vertex: state, stamp, two worklist
-//      entries) fits in the device arena (first-fit over free ranges); the
-//      arena is sized from free HBM when the server starts;
+//      the query's state (20 bytes per vertex: the packed (value, round id)
+//      word, the u32 result and two worklist entries) fits in the device arena
+//      (first-fit over free ranges); the arena is sized from free HBM when the
+//      server starts;
 //   2. upload the sorted descriptor table of the active queries and the new
 //      queries' sources; the admission kernels write their initial values and
 //      append their sources to the pending worklist, which still holds the
@@ -137,8 +138,9 @@ struct irgl_server {
   // device
   DevStatus* st = nullptr;
   DevStatus* st_host = nullptr;
-  uint32_t* state = nullptr;
-  uint32_t* stamp = nullptr;
+  uint32_t* state = nullptr;           // results (extracted from ds when a query finishes)
+  uint32_t* stamp = nullptr;           // two-array form only (IRGL_TUNE_NO_PACKED)
+  unsigned long long* ds = nullptr;    // packed (value, round id) arena
   uint32_t* items[2] = {nullptr, nullptr};
   uint32_t* qlast = nullptr;
   uint32_t* cont = nullptr;
@@ -195,6 +197,7 @@ void server_free(irgl_server* s) {
   cudaFree(s->st);
   cudaFree(s->state);
   cudaFree(s->stamp);
+  cudaFree(s->ds);
   cudaFree(s->items[0]);
   cudaFree(s->items[1]);
   cudaFree(s->qlast);
@@ -333,6 +336,7 @@ bool server_step(irgl_server* s) {
     ap.total = pre;
     ap.srcs = s->srcs;
     ap.state = s->state;
+    ap.ds = s->ds;
     ap.qlast = s->qlast;
     ap.items[0] = s->items[0];
     ap.items[1] = s->items[1];
@@ -364,6 +368,7 @@ bool server_step(irgl_server* s) {
   bp.nq = nq;
   bp.state = s->state;
   bp.stamp = s->stamp;
+  bp.ds = s->ds;
   bp.qlast = s->qlast;
   bp.items[0] = s->items[0];
   bp.items[1] = s->items[1];
@@ -412,6 +417,9 @@ bool server_step(irgl_server* s) {
   if (e == cudaSuccess) e = ensure_scratch(s, need);
   for (auto& a : fin) {
     uint32_t* dst = a.rq.host_out ? a.rq.host_out : s->h_scratch;
+    if (e == cudaSuccess && s->ds)
+      e = launch_extract_values(s->ds + a.base, s->state + a.base, a.n, static_cast<uint32_t>(s->ctx->sm_count) * 4,
+                                s->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dst, s->state + a.base, sizeof(uint32_t) * (size_t)a.n, cudaMemcpyDeviceToHost, s->stream);
     if (s->cfg.count_edges && e == cudaSuccess) {
@@ -503,7 +511,8 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
     cudaMemGetInfo(&fr, &tot);
     bytes = static_cast<uint64_t>(fr * 0.4);
   }
-  s->arena_n = std::min<uint64_t>(bytes / 16, 0xFFFFFFF0ull);
+  const bool packed = !(t.flags & IRGL_TUNE_NO_PACKED);
+  s->arena_n = std::min<uint64_t>(bytes / (packed ? 20 : 16), 0xFFFFFFF0ull);
   const uint32_t S = cfg->max_slots;
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&s->ev[0]);
@@ -511,7 +520,10 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   if (e == cudaSuccess) e = cudaMalloc(&s->st, sizeof(DevStatus));
   if (e == cudaSuccess) e = cudaMallocHost(&s->st_host, sizeof(DevStatus));
   if (e == cudaSuccess) e = cudaMalloc(&s->state, sizeof(uint32_t) * s->arena_n);
-  if (e == cudaSuccess) e = cudaMalloc(&s->stamp, sizeof(uint32_t) * s->arena_n);
+  if (e == cudaSuccess) {
+    if (packed) e = cudaMalloc(&s->ds, sizeof(unsigned long long) * s->arena_n);
+    else e = cudaMalloc(&s->stamp, sizeof(uint32_t) * s->arena_n);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&s->items[0], sizeof(uint32_t) * s->arena_n);
   if (e == cudaSuccess) e = cudaMalloc(&s->items[1], sizeof(uint32_t) * s->arena_n);
   if (e == cudaSuccess) e = cudaMalloc(&s->qlast, sizeof(uint32_t) * S);
@@ -541,7 +553,7 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   z.epoch = 1;
   *s->st_host = z;
   e = cudaMemcpyAsync(s->st, s->st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->stamp, 0, sizeof(uint32_t) * s->arena_n, s->stream);
+  if (e == cudaSuccess && s->stamp) e = cudaMemsetAsync(s->stamp, 0, sizeof(uint32_t) * s->arena_n, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->cont, 0, 128, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->qlast, 0, sizeof(uint32_t) * S, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);

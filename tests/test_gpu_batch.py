@@ -41,7 +41,8 @@ def _instances():
 
 @pytest.mark.parametrize("use_graph", [True, False])
 @pytest.mark.parametrize("tuning", [None, dict(cta_size=128, warp_thresh=4, cta_thresh=64, chunk=2),
-                                    dict(cta_size=512, warp_thresh=1 << 30, cta_thresh=1 << 30, max_blocks=5)])
+                                    dict(cta_size=512, warp_thresh=1 << 30, cta_thresh=1 << 30, max_blocks=5),
+                                    dict(cta_size=256, flags=8)])  # two-array arena (IRGL_TUNE_NO_PACKED)
 def test_batch_matches_oracle(ctx, use_graph, tuning):
     from paper_1607_05707_gb300.api import Batch
 

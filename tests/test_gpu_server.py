@@ -83,7 +83,7 @@ def test_server_admission_by_memory(env):
     ctx, graphs, dgs = env
     big = graphs[0].n  # 16384 vertices
     # arena of 1.5 large queries: queries queue until memory frees up, all still complete
-    srv = Server(ctx, arena_bytes=int(1.5 * big) * 16, max_slots=8, epoch_rounds=4)
+    srv = Server(ctx, arena_bytes=int(1.5 * big) * 20, max_slots=8, epoch_rounds=4)  # 20 bytes per arena entry
     qs = [("bfs", 0, int(s)) for s in inputs.sources(graphs[0], 6, seed=9)]
     bufs = [np.empty(big, dtype=np.uint32) for _ in qs]
     tickets = [srv.submit(k, dgs[gi], s, b) for (k, gi, s), b in zip(qs, bufs)]
