@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--slots", type=int, default=64,
                     help="serve: concurrent query slots (64 measured best: the active queries' state stays nearer L2)")
     ap.add_argument("--epoch-rounds", type=int, default=32, help="serve: rounds per epoch")
+    ap.add_argument("--arena-gb", type=float, default=0.0, help="serve: device arena budget (0: 40% of free HBM)")
     ap.add_argument("--verify", type=int, default=32, help="serve: queries checked against the oracle")
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (rmat20 workload)")
     ap.add_argument("--mesh-side", type=int, default=4096)
@@ -75,6 +76,9 @@ def parse_args():
     ap.add_argument("--trace", action="store_true", help="print a per-round trace of one query per kernel to stderr")
     ap.add_argument("--diropt", action="store_true",
                     help="BFS direction-optimising (bottom-up rounds on large frontiers; loads the in-edge CSR)")
+    ap.add_argument("--local", type=int, default=-1,
+                    help="CTA-local sub-rounds for persistent BFS/SSSP (0..15; default: 15 on the high-diameter "
+                         "grid64 and mesh workloads, 0 on R-MAT, as the autotuner picks them)")
     return ap.parse_args()
 
 
@@ -368,10 +372,15 @@ def run_gpu(args, world, rank, local):
     dg = ctx.load(g, validate=False, in_edges=args.diropt)
     out = {k: ctx.state(g.n) for k in kernels}
     ktune = {}
+    local_k = args.local if args.local >= 0 else (15 if args.workload in ("grid64", "mesh") else 0)
+    if args.diropt:
+        local_k = 0  # bottom-up rounds and CTA-local sub-rounds exclude each other
     for k in kernels:
         t = dict(tuning or {})
         if args.diropt and k == "bfs":
             t["flags"] = int(t.get("flags", 0)) | 2
+        if local_k and k in ("bfs", "sssp") and not (int(t.get("flags", 0)) >> 8) & 15:
+            t["flags"] = int(t.get("flags", 0)) | ((local_k & 15) << 8)
         if k == "cc" and args.cc_delta and "delta" not in t:
             t["delta"] = args.cc_delta
         ktune[k] = t or None
@@ -518,10 +527,11 @@ def run_gpu(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": round(1e3 * t_max / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": dict(workload=name, **meta, mode="persistent (iteration-outlined cooperative launch)"
-                           + (", BFS direction-optimising" if args.diropt else ""),
+                           + (", BFS direction-optimising" if args.diropt else "")
+                           + (f", {local_k} CTA-local sub-rounds per round" if local_k else ""),
                            parallelism=f"replicas x{world} (queries sharded, no collective)",
                            l2="flushed between steps (512 MB write, outside the events)",
-                           tuning=tuning or ctx.default_tuning),
+                           tuning={k: {**ctx.default_tuning, **(ktune[k] or {})} for k in kernels}),
             "e2e": {"value": round(e2e_val, 4), "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(kernels),
                     "d2h_bytes_per_step": 4 * g.n * len(kernels)},
             "gpu_launches": launches_per_step * args.steps,
@@ -701,8 +711,8 @@ def run_serve(args, world, rank, local):
         srcs[i] = v
     verify = set(rng.choice(nq, size=min(args.verify, nq), replace=False).tolist())
     bufs = {i: np.empty(graphs[gi[i]].n, dtype=np.uint32) for i in verify}
-    srv = Server(ctx, arena_bytes=0, max_slots=args.slots, epoch_rounds=args.epoch_rounds, count_edges=True,
-                 tuning=tuning)
+    srv = Server(ctx, arena_bytes=int(args.arena_gb * (1 << 30)), max_slots=args.slots,
+                 epoch_rounds=args.epoch_rounds, count_edges=True, tuning=tuning)
     # warm-up: a few queries before the clock starts
     for i in range(min(8, nq)):
         srv.submit(kinds[i], dgs[gi[i]], int(srcs[i]))

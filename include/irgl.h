@@ -104,6 +104,15 @@ typedef struct {
                                  through L1, filters edges to visited vertices before the level is
                                  read from L2 (off by default: slower on R-MAT scale 20, where the
                                  bit updates cost more than the L2 reads they save) */
+#define IRGL_TUNE_LOCAL(k) (((uint32_t)(k) & 15u) << 8) /* persistent BFS and SSSP: after its tiles,
+                                    each CTA expands the vertices it just discovered k more times (CTA-local
+                                    sub-rounds, CTA barriers only) before flushing the rest to the
+                                    out-worklist, so high-diameter graphs need fewer grid barriers; BFS
+                                    then runs as unit-weight label-correcting relaxation (same levels).
+                                    Pays on high-diameter graphs (meshes, grids), costs extra work on
+                                    low-diameter ones (R-MAT); irgl_autotune tries k = 0, 4, 15.
+                                    max_rounds is capped at 2^32 / (k + 1) - 1 global rounds.
+                                    Ignored with IRGL_TUNE_DIROPT or IRGL_TUNE_NO_PACKED. */
 #define IRGL_TUNE_NO_PACKED 0x8u /* persistent SSSP: keep distances and the dedup stamps in two
                                     arrays (by default one 64-bit word per vertex holds both,
                                     lowered by one atomicMin, and the distances are copied to the
@@ -250,7 +259,9 @@ irgl_status irgl_control_cta(const uint32_t* masks, uint32_t count, uint32_t pre
 
 /* ---------------------------------------------------------------- autotuning
  * Coordinate descent over the irgl_tuning fields (CTA size, CTA and warp
- * degree thresholds, chunk, CTAs per SM), each candidate timed as the median
+ * degree thresholds, chunk, CTAs per SM; for BFS and SSSP also the CTA-local
+ * sub-rounds, flags = IRGL_TUNE_LOCAL(0, 4 or 15); for SSSP also the near-far
+ * delta), each candidate timed as the median
  * CUDA-event time of `reps` persistent Iterate runs of kernel k from the given
  * sources on graph g (after one warm-up run). *best receives the fastest
  * tuning and *best_ms its time. Results do not depend on the tuning (the

@@ -154,6 +154,11 @@ class Context:
         st = C.irgl_msf(self.handle, g.handle, C.MODES[mode], C.LOCKS[lock], _np_ptr(buf), buf.size, 1, tuning)
         return buf[: st["edges"]].copy(), st
 
+    def autotune(self, kernel: str, g: Graph, srcs=None, reps: int = 3) -> tuple[dict, float]:
+        """Fastest tuning for persistent runs of `kernel` from `srcs` on g, and its median ms."""
+        s = None if srcs is None else np.ascontiguousarray(np.atleast_1d(srcs), dtype=np.uint32)
+        return C.irgl_autotune(self.handle, C.KERNELS[kernel], g.handle, _np_ptr(s), 0 if s is None else s.size, reps)
+
     def init_state(self, kernel: str, g: Graph, initial: Worklist | None, state: torch.Tensor) -> None:
         C.irgl_init_state(self.handle, C.KERNELS[kernel], g.handle, None if initial is None else initial.handle,
                           state.data_ptr())
@@ -196,6 +201,10 @@ class Batch:
     def prepare(self, tuning=None, use_cuda_graph: bool = True) -> dict:
         C.irgl_batch_prepare(self.handle, tuning, 1 if use_cuda_graph else 0)
         return C.irgl_batch_info(self.handle)
+
+    def autotune(self, reps: int = 3) -> tuple[dict, float]:
+        """Fastest tuning for this batch (prepared with it afterwards) and its median ms."""
+        return C.irgl_batch_autotune(self.handle, reps)
 
     def launch(self) -> None:
         C.irgl_batch_launch(self.handle)

@@ -138,7 +138,8 @@ cudaError_t alloc_big(uint32_t cap, uint4** e, unsigned long long** off) {
   return r;
 }
 
-irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool need_far, bool need_vis, bool need_ds) {
+irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool need_far, bool need_vis, bool need_ds,
+                             uint32_t wl_mult) {
   if (need_far && n > ctx->ws_far_n) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->ws_far[0]);
@@ -165,7 +166,8 @@ irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool ne
     if (e != cudaSuccess) return cuda_fail(e, "big-list allocation");
     ctx->big_cap = bcap;
   }
-  uint32_t cap = ctx->dbg_cap ? ctx->dbg_cap : std::max<uint32_t>(n, 1);
+  const uint64_t want = std::max<uint64_t>(static_cast<uint64_t>(n) * std::max<uint32_t>(wl_mult, 1u), 1);
+  uint32_t cap = ctx->dbg_cap ? ctx->dbg_cap : static_cast<uint32_t>(std::min<uint64_t>(want, 0xFFFFFFF0ull));
   if (cap > ctx->ws_cap || ctx->dbg_cap) {
     if (ctx->ws_items[0] || ctx->ws_items[1]) {
       cudaStreamSynchronize(ctx->stream);
@@ -757,12 +759,19 @@ irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workl
   s = resolve_tuning(tin, &t);
   if (s != IRGL_OK) return s;
   DeviceGuard guard(ctx->device);
-  const bool vis = k == IRGL_BFS && mode == IRGL_PERSISTENT && (t.flags & IRGL_TUNE_BITMAP);
-  const bool packed = k == IRGL_SSSP && mode == IRGL_PERSISTENT && !(t.flags & IRGL_TUNE_NO_PACKED);
+  // CTA-local sub-rounds (persistent BFS and SSSP on packed words, plain rounds)
+  const uint32_t sub_rounds = (t.flags >> 8) & 15u;
+  const bool use_local = mode == IRGL_PERSISTENT && sub_rounds != 0 && !(t.flags & IRGL_TUNE_NO_PACKED) &&
+                         ((k == IRGL_SSSP && t.delta == 0) ||
+                          (k == IRGL_BFS && !(t.flags & (IRGL_TUNE_DIROPT | IRGL_TUNE_BITMAP))));
+  const bool vis = k == IRGL_BFS && mode == IRGL_PERSISTENT && (t.flags & IRGL_TUNE_BITMAP) && !use_local;
+  const bool packed = (k == IRGL_SSSP || (k == IRGL_BFS && use_local)) && mode == IRGL_PERSISTENT &&
+                      !(t.flags & IRGL_TUNE_NO_PACKED);
   const bool far = (k == IRGL_SSSP || k == IRGL_CC) && mode == IRGL_PERSISTENT && t.delta != 0;
-  s = ensure_workspace(ctx, g->n, k != IRGL_BFS, far, vis, packed);
+  // a vertex can be pushed once per sub-round: worklists of n * (sub-rounds + 1)
+  s = ensure_workspace(ctx, g->n, k != IRGL_BFS, far, vis, packed, use_local ? sub_rounds + 1u : 1u);
   if (s != IRGL_OK) return s;
-  const uint32_t op = op_of(k);
+  const uint32_t op = (use_local && k == IRGL_BFS) ? OP_BFSR : op_of(k);
   if (k == IRGL_CC_JUMP && mode != IRGL_PERSISTENT)
     return fail(IRGL_ERR_UNSUPPORTED, "pointer-jumping CC runs only as a persistent Iterate");
   KParams p = make_params(ctx, g, state_dev, t);
@@ -772,6 +781,13 @@ irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workl
   p.max_rounds = max_rounds ? max_rounds : 0xFFFFFFFFu;
   if (vis) p.vis = ctx->ws_vis;
   if (packed) p.ds = ctx->ws_ds;
+  if (use_local) {
+    p.local_rounds = sub_rounds;
+    p.diropt = 0;
+    // round r stamps with ids r * (sub-rounds + 1) + 1 .. (r + 1) * (sub-rounds + 1):
+    // stop before they would wrap to 0, the "on no worklist" stamp
+    p.max_rounds = std::min(p.max_rounds, 0xFFFFFFFFu / (sub_rounds + 1u) - 1u);
+  }
   irgl_stats local;
   std::memset(&local, 0, sizeof(local));
   local.cta_size = t.cta_size;

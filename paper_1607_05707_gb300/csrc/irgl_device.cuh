@@ -33,7 +33,10 @@ constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Operator ids (OP_RUNTIME: taken per query from the batch descriptor).
-enum : uint32_t { OP_BFS = 0, OP_SSSP = 1, OP_CC = 2, OP_RUNTIME = 3, OP_CCJ = 4 };
+// OP_BFSR: BFS levels by label-correcting relaxation (SSSP with unit weights:
+// a popped vertex's current level + 1), the form the CTA-local sub-rounds need,
+// since a vertex can be reached there before its level is final.
+enum : uint32_t { OP_BFS = 0, OP_SSSP = 1, OP_CC = 2, OP_RUNTIME = 3, OP_CCJ = 4, OP_BFSR = 5 };
 
 // Operators whose values can be scheduled near-far (smallest first): SSSP
 // distances and min-label CC labels.
@@ -43,7 +46,7 @@ constexpr bool kNearFarOp = OP == OP_SSSP || OP == OP_CC;
 // Operators that can keep (value, round id) in one 64-bit word per vertex:
 // single-graph SSSP, and every query of the batched kernel.
 template <uint32_t OP>
-constexpr bool kPackedOp = OP == OP_SSSP || OP == OP_RUNTIME;
+constexpr bool kPackedOp = OP == OP_SSSP || OP == OP_RUNTIME || OP == OP_BFSR;
 enum : int { RED_NONE = 0, RED_ANY = 1, RED_ALL = 2 };
 // Device error codes (first one wins).
 enum : uint32_t {
@@ -166,6 +169,10 @@ struct KParams {
   // words, filled in the prologue and copied out to `state` at the end;
   // nullptr = dist in `state` and dedup stamps in `stamp`
   unsigned long long* ds;
+  // CTA-local sub-rounds per round (packed relaxations only; 0 = off): after
+  // its tiles a CTA expands what it pushed to its shared-memory stage, up to
+  // this many more times, before flushing the rest to the out-worklist
+  uint32_t local_rounds;
 };
 
 // Per-launch (one round) arguments.
@@ -327,9 +334,17 @@ struct BatchSmem {
 // Flush the stage to the out-worklist: one global atomicAdd, coalesced stores.
 // Called by every thread of the CTA at a CTA-uniform point, after a barrier.
 template <int CTA>
-__device__ __forceinline__ void flush_stage(Smem<CTA>& sm, const Out& out) {
-  const uint32_t n = min(sm.stage_n, static_cast<uint32_t>(Smem<CTA>::kStage));
-  if (n == 0) return;
+__device__ __forceinline__ void flush_stage(Smem<CTA>& sm, const Out& out, uint32_t from = 0) {
+  const uint32_t end = min(sm.stage_n, static_cast<uint32_t>(Smem<CTA>::kStage));
+  const uint32_t n = end > from ? end - from : 0u;
+  if (n == 0) {
+    if (from != 0) {  // the stage held only expanded items: empty it
+      __syncthreads();
+      if (threadIdx.x == 0) sm.stage_n = 0;
+      __syncthreads();
+    }
+    return;
+  }
   if (threadIdx.x == 0) {
     sm.gbase = atomicAdd(out.tail, n);
     sm.round_pushes += n;
@@ -338,7 +353,7 @@ __device__ __forceinline__ void flush_stage(Smem<CTA>& sm, const Out& out) {
   const uint32_t gb = sm.gbase;
   for (uint32_t i = threadIdx.x; i < n; i += CTA) {
     const uint32_t idx = gb + i;
-    if (idx < out.cap) __stcg(out.items + idx, sm.stage[i]);
+    if (idx < out.cap) __stcg(out.items + idx, sm.stage[from + i]);
     else set_err(out.err, DERR_WL_OVERFLOW);
   }
   __syncthreads();
@@ -591,6 +606,8 @@ struct RoundCtx {
   uint32_t* vis;                  // BFS visited bitmap, or nullptr
   unsigned long long* ds;         // SSSP packed (dist, round id) words, or nullptr
   uint32_t dsr;                   //   and this round's id in them (1, 2, ...)
+  uint32_t local_rounds;          // CTA-local sub-rounds after the tiles (0 = none)
+  const uint32_t* local_items;    // a sub-round's items: a range of the CTA's stage (shared memory)
 };
 
 // The destination's current value as the operator reads it. BFS with the
@@ -632,7 +649,7 @@ __device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state
     // pushed by the thread that lowers it first in this round (a far
     // improvement stamps 0: see decide_n). BFS levels are lowered from INF.
     const uint32_t o = OP == OP_RUNTIME ? op_rt : OP;
-    const uint32_t nd = o == OP_SSSP ? val + static_cast<uint32_t>(wt) : val;
+    const uint32_t nd = o == OP_SSSP ? val + static_cast<uint32_t>(wt) : (o == OP_BFSR ? val + 1u : val);
     if (o == OP_BFS ? cur != kInf : nd >= cur) return 0u;
     const bool far = OP == OP_SSSP && rc.limit != kInf && nd >= rc.limit;
     const unsigned long long old =
@@ -677,7 +694,7 @@ __device__ __forceinline__ void decide_n(const RoundCtx& rc, uint32_t* state, ui
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const uint32_t o = OP == OP_RUNTIME ? op[k] : OP;
-    nd[k] = o == OP_SSSP ? val[k] + static_cast<uint32_t>(wt[k]) : val[k];
+    nd[k] = o == OP_SSSP ? val[k] + static_cast<uint32_t>(wt[k]) : (o == OP_BFSR ? val[k] + 1u : val[k]);
     t[k] = ((valid >> k) & 1u) != 0 && (o == OP_BFS ? cur[k] == kInf : nd[k] < cur[k]);
   }
   // near-far: an improvement to a value >= the limit goes to the far list,
@@ -855,7 +872,7 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
   bool valid = idx < rc.in_n;
   uint32_t q = 0, beg = 0, end = 0, val = 0;
   if (valid) {
-    const uint32_t item = rc.in_items ? __ldcg(rc.in_items + idx) : idx;
+    const uint32_t item = rc.local_items ? rc.local_items[idx] : (rc.in_items ? __ldcg(rc.in_items + idx) : idx);
     uint32_t u;
     g.decode(item, q, u);
     if (u >= g.nverts(q)) {  // a caller-pushed item outside the graph: report and skip it
@@ -866,7 +883,13 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
       beg = __ldg(rp + u);
       end = __ldg(rp + u + 1);
       const uint32_t op = g.op(q);
-      if (kPackedOp<OP> && rc.ds != nullptr && (OP != OP_RUNTIME || op != OP_BFS))
+      if (kPackedOp<OP> && rc.ds != nullptr && rc.local_items != nullptr)
+        // a CTA-local pop: take the value and clear the round stamp in one
+        // atomic, so an improvement that lands after this read (from any CTA,
+        // in any sub-round) pushes the vertex again instead of counting on a
+        // pending expansion that has just happened
+        val = static_cast<uint32_t>(atomicAnd(rc.ds + item, 0xFFFFFFFF00000000ull) >> 32);
+      else if (kPackedOp<OP> && rc.ds != nullptr && (OP != OP_RUNTIME || op != OP_BFS))
         val = static_cast<uint32_t>(__ldcg(rc.ds + item) >> 32);
       else if (op == OP_BFS)
         val = !V::kBatched ? rc.bfs_val
@@ -1008,7 +1031,9 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
   }
 
   if (RED == RED_ANY) any_true |= pushed ? 1u : 0u;
-  const bool full = __syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2));
+  // a sub-round reads its items from the stage: no flush may move them under it
+  const bool full = __syncthreads_or(rc.local_items == nullptr &&
+                                     sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2));
   if (RED == RED_ALL) {
     if (valid && !sm.pushed[tid]) any_false = 1u;
     sm.pushed[tid] = 0;
@@ -1038,8 +1063,30 @@ __device__ __forceinline__ void round_body(const V& g, Smem<CTA>& sm, const Roun
     __syncthreads();
     gb = sm.grab_base;
   }
+  // CTA-local sub-rounds: expand the stage's newest items [lo, hi) here, with
+  // CTA barriers only; their pushes land after them in the stage (or go global
+  // when it is full). A round stamp still means "waiting on a worklist": each
+  // sub-round stamps with its own id, and a local pop clears the stamp (see
+  // process_tile), so every improvement that an expansion may have missed
+  // pushes the vertex again; the relaxation is label-correcting, so the fixed
+  // point is the same. What is left unexpanded is flushed to the out-worklist.
+  uint32_t lo = 0;
+  if (kPackedOp<OP> && !V::kBatched && rc.local_rounds != 0) {
+    RoundCtx lc = rc;
+    for (uint32_t j = 1; j <= rc.local_rounds; ++j) {
+      __syncthreads();
+      const uint32_t hi = min(sm.stage_n, static_cast<uint32_t>(Smem<CTA>::kStage));
+      if (hi <= lo || hi >= static_cast<uint32_t>(Smem<CTA>::kStage)) break;  // nothing new, or the stage is full
+      lc.local_items = sm.stage + lo;
+      lc.in_n = hi - lo;
+      lc.dsr = rc.dsr + j;
+      for (uint32_t t = 0; t < hi - lo; t += CTA)
+        process_tile<OP, CTA, RED>(g, sm, lc, t + threadIdx.x, edges, any_true, any_false);
+      lo = hi;
+    }
+  }
   __syncthreads();
-  flush_stage<CTA>(sm, rc.out);
+  flush_stage<CTA>(sm, rc.out, lo);
 }
 
 // ----------------------------------------------------------------------------- grid barrier
@@ -1463,7 +1510,7 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
 #pragma unroll
     for (uint32_t i = 0; i < 8; ++i) srcs[i] = (small && i < init_n) ? __ldcg(p.init_items + i) : kInf;
     if (small) ns = init_n;
-    if (OP == OP_SSSP && p.ds != nullptr) fill_packed(p.ds, p.n, srcs, ns, blockIdx.x * CTA + threadIdx.x, gridDim.x * CTA);
+    if ((OP == OP_SSSP || OP == OP_BFSR) && p.ds != nullptr) fill_packed(p.ds, p.n, srcs, ns, blockIdx.x * CTA + threadIdx.x, gridDim.x * CTA);
     else fill_state<OP>(p.state, p.n, srcs, ns, blockIdx.x * CTA + threadIdx.x, gridDim.x * CTA);
     if (OP != OP_CC && !small) {
       ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
@@ -1471,12 +1518,12 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
         for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < init_n; i += gridDim.x * CTA) {
           const uint32_t s = p.init_items ? __ldcg(p.init_items + i) : i;
           if (s >= p.n) continue;
-          if (OP == OP_SSSP && p.ds != nullptr) __stcg(p.ds + s, 0ull);
+          if ((OP == OP_SSSP || OP == OP_BFSR) && p.ds != nullptr) __stcg(p.ds + s, 0ull);
           else __stcg(p.state + s, 0u);
         }
       }
     }
-  } else if (OP == OP_SSSP && p.ds != nullptr) {
+  } else if ((OP == OP_SSSP || OP == OP_BFSR) && p.ds != nullptr) {
     // the caller's initial distances, round id 0
     for (uint32_t v = blockIdx.x * CTA + threadIdx.x; v < p.n; v += gridDim.x * CTA)
       __stcg(p.ds + v, static_cast<unsigned long long>(__ldcg(p.state + v)) << 32);
@@ -1525,8 +1572,10 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     rc.mf = dopt ? &sm.mf_cta : nullptr;
     rc.row_ptr = p.row_ptr;
     rc.vis = OP == OP_BFS ? p.vis : nullptr;
-    rc.ds = OP == OP_SSSP ? p.ds : nullptr;
-    rc.dsr = r + 1u;
+    rc.ds = (OP == OP_SSSP || OP == OP_BFSR) ? p.ds : nullptr;
+    rc.dsr = r * (p.local_rounds + 1u) + 1u;  // room for the sub-rounds' ids
+    rc.local_rounds = (OP == OP_SSSP || OP == OP_BFSR) ? p.local_rounds : 0u;
+    rc.local_items = nullptr;
     const uint32_t ftarget = split ? (fb ^ 1u) : fb;  // far list this round pushes to
     rc.far_out = Out{ftarget ? p.far[1] : p.far[0], &st->far_tail[ftarget], p.far_cap, &st->err};
     if (threadIdx.x == 0) {
@@ -1618,7 +1667,7 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     }
     in_n = min(last_out, p.cap);
   }
-  if (OP == OP_SSSP && p.ds != nullptr) {
+  if ((OP == OP_SSSP || OP == OP_BFSR) && p.ds != nullptr) {
     // every round ended at a barrier that all CTAs passed: the words are final
     for (uint32_t v = blockIdx.x * CTA + threadIdx.x; v < p.n; v += gridDim.x * CTA)
       __stcg(p.state + v, static_cast<uint32_t>(__ldcg(p.ds + v) >> 32));
@@ -1669,6 +1718,8 @@ __device__ __forceinline__ void cc_jump_persistent(const KParams& p, Smem<CTA>& 
     rc.vis = nullptr;
     rc.ds = nullptr;
     rc.dsr = 0;
+    rc.local_rounds = 0;
+    rc.local_items = nullptr;
     if (threadIdx.x == 0) {
       if (blockIdx.x == 0) {
         st->tail[(r + 2) % 3] = 0;
@@ -1738,6 +1789,8 @@ __device__ __forceinline__ void invoke_round(const KParams& p, const RoundArgs& 
   rc.vis = nullptr;
   rc.ds = nullptr;
   rc.dsr = 0;
+  rc.local_rounds = 0;
+  rc.local_items = nullptr;
   uint32_t edges = 0, any_true = 0, any_false = 0;
   round_body<OP, CTA, RED>(g, sm, rc, edges, any_true, any_false);
   const int t = __syncthreads_or(any_true != 0);
@@ -1834,6 +1887,8 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
     rc.vis = nullptr;
     rc.ds = p.ds;     // round ids are the global ones: admission writes id 0
     rc.dsr = rc.ep;
+    rc.local_rounds = 0;
+    rc.local_items = nullptr;
     if (threadIdx.x == 0) {
       if (blockIdx.x == 0) {
         st->tail[(r + 2) % 3] = 0;

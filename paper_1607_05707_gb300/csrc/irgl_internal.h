@@ -93,7 +93,7 @@ irgl_status status_from_device(const DevStatus& s);
 irgl_status control_cta(const uint32_t* masks, uint32_t count, uint32_t preferred, uint32_t* out);
 void reset_status(irgl_ctx* ctx);
 irgl_status ensure_workspace(irgl_ctx* ctx, uint32_t n, bool need_stamp, bool need_far = false,
-                             bool need_vis = false, bool need_ds = false);
+                             bool need_vis = false, bool need_ds = false, uint32_t wl_mult = 1);
 uint32_t big_capacity(uint64_t n);
 cudaError_t alloc_big(uint32_t cap, uint4** e, unsigned long long** off);
 int occupancy(irgl_ctx* ctx, int kind, uint32_t op, uint32_t cta, int red);
@@ -102,7 +102,7 @@ irgl_status check_kernel_graph(irgl_kernel k, const irgl_graph* g);
 uint32_t op_of(irgl_kernel k);
 KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tuning& t);
 irgl_status tune_descend(const std::function<float(const irgl_tuning&)>& measure, irgl_tuning* best, float* best_ms,
-                         bool with_delta = false);
+                         bool with_delta = false, bool with_local = false);
 
 }  // namespace irgl
 

@@ -1,4 +1,4 @@
-// Persistent cooperative Iterate kernels: BFS / SSSP / CC / pointer-jumping CC x CTA size.
+// Persistent cooperative Iterate kernels: BFS / SSSP / CC / pointer-jumping CC / BFS by relaxation x CTA size.
 #include <algorithm>
 
 #include "irgl_launch.h"
@@ -88,6 +88,7 @@ cudaError_t launch_iterate(uint32_t op, uint32_t cta, uint32_t grid, const KPara
     case OP_SSSP: return launch_op<OP_SSSP>(cta, grid, p, s);
     case OP_CC: return launch_op<OP_CC>(cta, grid, p, s);
     case OP_CCJ: return launch_op<OP_CCJ>(cta, grid, p, s);
+    case OP_BFSR: return launch_op<OP_BFSR>(cta, grid, p, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -98,6 +99,7 @@ cudaError_t occupancy_iterate(uint32_t op, uint32_t cta, int* nb) {
     case OP_SSSP: return occ_op<OP_SSSP>(cta, nb);
     case OP_CC: return occ_op<OP_CC>(cta, nb);
     case OP_CCJ: return occ_op<OP_CCJ>(cta, nb);
+    case OP_BFSR: return occ_op<OP_BFSR>(cta, nb);
   }
   return cudaErrorInvalidValue;
 }

@@ -21,7 +21,7 @@ struct Axis {
   std::vector<uint32_t> values;
 };
 
-std::vector<Axis> axes(bool with_delta) {
+std::vector<Axis> axes(bool with_delta, bool with_local) {
   std::vector<Axis> a = {
       {&irgl_tuning::cta_size, {128, 256, 512, 1024}},
       {&irgl_tuning::cta_thresh, {32, 64, 128, 256, 512, 1024, 4096}},
@@ -30,6 +30,8 @@ std::vector<Axis> axes(bool with_delta) {
       {&irgl_tuning::blocks_per_sm, {0, 1, 2, 4}},
   };
   if (with_delta) a.push_back({&irgl_tuning::delta, {0, 16, 32, 64, 128, 256, 512}});
+  // CTA-local sub-rounds; the only flag the search sets (the defaults have none)
+  if (with_local) a.push_back({&irgl_tuning::flags, {0, IRGL_TUNE_LOCAL(4), IRGL_TUNE_LOCAL(15)}});
   return a;
 }
 
@@ -37,13 +39,13 @@ std::vector<Axis> axes(bool with_delta) {
 
 // Coordinate descent; `measure` returns the median ms of one candidate (< 0: invalid).
 irgl_status irgl::tune_descend(const std::function<float(const irgl_tuning&)>& measure, irgl_tuning* best, float* best_ms,
-                                bool with_delta) {
+                                bool with_delta, bool with_local) {
   irgl_tuning cur = default_tuning();
   float cur_ms = measure(cur);
   if (cur_ms < 0) return fail(IRGL_ERR_CUDA, "autotune: default tuning failed: %s", g_last_error.c_str());
   for (int pass = 0; pass < 2; ++pass) {
     bool moved = false;
-    for (const Axis& ax : axes(with_delta)) {
+    for (const Axis& ax : axes(with_delta, with_local)) {
       for (uint32_t v : ax.values) {
         if (cur.*(ax.field) == v) continue;
         irgl_tuning cand = cur;
@@ -122,7 +124,7 @@ irgl_status irgl_autotune(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uin
     }
     return median(ms);
   };
-  s = tune_descend(measure, best, best_ms, k == IRGL_SSSP);
+  s = tune_descend(measure, best, best_ms, k == IRGL_SSSP, k == IRGL_BFS || k == IRGL_SSSP);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return s;

@@ -46,6 +46,11 @@ IRGL_TUNE_DIROPT = 0x2
 IRGL_TUNE_BITMAP = 0x4
 IRGL_TUNE_NO_PACKED = 0x8
 
+
+def IRGL_TUNE_LOCAL(k: int) -> int:
+    """Flag bits of k CTA-local sub-rounds (0..15)."""
+    return (int(k) & 15) << 8
+
 KERNELS = {"bfs": IRGL_BFS, "sssp": IRGL_SSSP, "cc": IRGL_CC, "cc_jump": IRGL_CC_JUMP}
 MODES = {"per_launch": IRGL_PER_LAUNCH, "persistent": IRGL_PERSISTENT}
 

@@ -414,6 +414,48 @@ def test_bottom_up_every_round(ctx):
         ctx.debug_set(5, 0)
 
 
+LOCAL = [dict(flags=1 << 8), dict(flags=4 << 8), dict(flags=15 << 8), dict(cta_size=1024, flags=8 << 8),
+         dict(cta_size=128, warp_thresh=1 << 30, cta_thresh=1 << 30, flags=3 << 8),
+         dict(cta_size=256, warp_thresh=2, cta_thresh=8, flags=4 << 8)]
+
+
+@pytest.mark.parametrize("tuning", LOCAL)
+def test_cta_local_sub_rounds(ctx, tuning):
+    """CTA-local sub-rounds (IRGL_TUNE_LOCAL(k)): BFS runs as unit-weight
+    label-correcting relaxation, SSSP keeps its operator; a CTA expands its own
+    fresh pushes k more times between grid barriers. Same levels and distances
+    on tiny, high-diameter and power-law graphs, single and multiple sources."""
+    rng = np.random.default_rng(71)
+    for trial in range(10):
+        n = int(rng.integers(1, 160))
+        g = tiny_graph(rng, n, float(rng.choice([0.02, 0.08])), bool(trial % 2))
+        dg = ctx.load(g)
+        srcs = rng.integers(0, n, size=int(rng.integers(1, 4))).astype(np.uint32)
+        check(ctx, "bfs", g, dg, srcs, "persistent", tuning)
+        check(ctx, "sssp", g, dg, srcs, "persistent", tuning)
+        dg.close()
+    m = inputs.mesh(300, 257, seed=72, del_frac=0.02, extra_frac=0.002, weights=True)
+    dm = ctx.load(m)
+    for srcs in ([0], [40000, 7]):
+        s = np.array(srcs, np.uint32)
+        st = check(ctx, "bfs", m, dm, s, "persistent", tuning)
+        check(ctx, "sssp", m, dm, s, "persistent", tuning)
+    dm.close()
+    r = inputs.rmat(15, 16, seed=73, weights=True)
+    dr = ctx.load(r)
+    for s in inputs.sources(r, 2, seed=74):
+        check(ctx, "bfs", r, dr, np.array([s], np.uint32), "persistent", tuning)
+        check(ctx, "sssp", r, dr, np.array([s], np.uint32), "persistent", tuning)
+    dr.close()
+    g, srcs = inputs.workload_grid64()
+    dg = ctx.load(g)
+    got, st = run(ctx, "bfs", g, dg, srcs, "persistent", tuning)
+    rr, cc = np.divmod(np.arange(g.n), 64)
+    np.testing.assert_array_equal(got, (rr + cc).astype(np.uint32))
+    assert st["rounds"] <= 127  # never more grid rounds than levels
+    dg.close()
+
+
 def test_bfs_visited_bitmap(ctx):
     """The persistent BFS visited bitmap (IRGL_TUNE_BITMAP = 4) gives the same
     levels; it is cleared per launch, so a graph run after a larger one (whose
@@ -460,6 +502,20 @@ def test_mesh4096_cc_near_far_full(ctx):
     st = check(ctx, "cc", g, dg, None, "persistent", dict(delta=1))
     assert st["edges_scanned"] <= 3 * g.m
     dg.close()
+
+
+def test_mesh4096_local_sub_rounds_full(ctx):
+    g, srcs = inputs.workload_mesh(4096)
+    dg = ctx.load(g, validate=False)
+    st = check(ctx, "bfs", g, dg, srcs, "persistent", dict(flags=8 << 8))
+    assert st["rounds"] < 7211  # fewer grid barriers than BFS levels
+    dg.close()
+    r, rs = inputs.workload_rmat20(nsrc=1)
+    dr = ctx.load(r, validate=False)
+    one = np.array([rs[0]], np.uint32)
+    check(ctx, "bfs", r, dr, one, "persistent", dict(flags=4 << 8))
+    check(ctx, "sssp", r, dr, one, "persistent", dict(flags=4 << 8))
+    dr.close()
 
 
 def test_mesh4096_bfs_full(ctx):
