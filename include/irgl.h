@@ -271,7 +271,7 @@ irgl_status irgl_autotune(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uin
 
 /* ---------------------------------------------------------------- batching
  * A batch runs many independent queries ("instances": a graph, a kernel and
- * its sources) in ONE persistent cooperative launch. Each instance owns a
+ * its sources) in one persistent cooperative launch per wave (below). Each instance owns a
  * range of a device state arena (its result), its worklist items travel on the
  * shared double-buffered worklist as arena offsets that a sorted offset table
  * maps back to the instance, and its termination flag is the round of its
@@ -292,6 +292,16 @@ irgl_status irgl_batch_destroy(irgl_batch* b);
 irgl_status irgl_batch_add(irgl_batch* b, irgl_graph* g, irgl_kernel k, const uint32_t* srcs_host, uint32_t nsrc,
                            uint32_t* query_id);
 irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* t, int use_cuda_graph);
+/* Waves: prepare splits the queries, in add order, into consecutive groups
+ * whose packed state (8 bytes per vertex) fits in `bytes`; a run admits and
+ * iterates one group after another (one persistent launch each, all in the
+ * same CUDA graph), so the random state accesses of the active group hit L2
+ * instead of DRAM. 0 (the default) = half the device's L2; UINT64_MAX = one
+ * wave (every query active at once). A query larger than `bytes` is a wave of
+ * its own. Takes effect at the next irgl_batch_prepare. The per-query rounds
+ * count the rounds of the query's own wave; stats->rounds sums the waves. */
+irgl_status irgl_batch_set_wave_bytes(irgl_batch* b, uint64_t bytes);
+irgl_status irgl_batch_waves(irgl_batch* b, uint32_t* waves);
 /* Enqueue one run (events bracket it); irgl_batch_sync waits, checks the device
  * status and fills stats (device_ms = event time of the run). */
 irgl_status irgl_batch_launch(irgl_batch* b);
@@ -303,6 +313,11 @@ irgl_status irgl_batch_info(irgl_batch* b, uint32_t* nqueries, uint32_t* grid, u
  * destroy) and the rounds that query was active (from its termination flag). */
 irgl_status irgl_batch_result(irgl_batch* b, uint32_t query_id, uint32_t** state_dev, uint32_t* n, uint32_t* rounds);
 irgl_status irgl_batch_copy_result(irgl_batch* b, uint32_t query_id, uint32_t* host_out);
+/* Every query's result in one transfer: host_out (arena_entries values, see
+ * irgl_batch_info) receives the queries' results back to back in add order
+ * (query q at the sum of n over the queries added before it). Pinned host
+ * memory makes the copy asynchronous to the CPU; it completes before return. */
+irgl_status irgl_batch_copy_results(irgl_batch* b, uint32_t* host_out);
 /* Autotune a prepared batch: the same coordinate descent, each candidate timed
  * as the median event time of `reps` whole-batch runs (the batch is re-prepared
  * per candidate, with the CUDA-graph choice it was prepared with). The batch is

@@ -198,7 +198,10 @@ class Batch:
         self.sizes.append(g.n)
         return q
 
-    def prepare(self, tuning=None, use_cuda_graph: bool = True) -> dict:
+    def prepare(self, tuning=None, use_cuda_graph: bool = True, wave_bytes: int | None = None) -> dict:
+        """wave_bytes: packed-state budget of one wave (0 = half the L2, 2**64 - 1 = one wave)."""
+        if wave_bytes is not None:
+            C.irgl_batch_set_wave_bytes(self.handle, wave_bytes)
         C.irgl_batch_prepare(self.handle, tuning, 1 if use_cuda_graph else 0)
         return C.irgl_batch_info(self.handle)
 
@@ -221,6 +224,16 @@ class Batch:
         out = np.empty(max(n, 1), dtype=np.uint32)
         C.irgl_batch_copy_result(self.handle, q, _np_ptr(out))
         return out[:n], rounds
+
+    def results(self, out: np.ndarray | None = None) -> list[np.ndarray]:
+        """Every query's result from one device-to-host copy (views into `out`, add order)."""
+        total = sum(self.sizes)
+        out = np.empty(max(total, 1), dtype=np.uint32) if out is None else out
+        if out.dtype != np.uint32 or out.size < total or not out.flags.c_contiguous:
+            raise ValueError(f"out must be a contiguous uint32 array of at least {total} entries")
+        C.irgl_batch_copy_results(self.handle, _np_ptr(out))
+        offs = np.cumsum([0] + self.sizes)
+        return [out[offs[i]:offs[i + 1]] for i in range(len(self.sizes))]
 
     def close(self) -> None:
         if self.handle:

@@ -1,6 +1,12 @@
 // Batching: many independent queries (instances) in one persistent cooperative
 // launch, captured once in a CUDA graph and replayed.
 //
+// Waves: the queries are split, in add order, into consecutive groups whose
+// packed state fits in a byte budget (default half the L2); a run admits and
+// iterates one group after another, each one persistent launch, so the random
+// state accesses of the active group stay in L2 (256 R-MAT instances of 16.4 M
+// vertices in all: 8.4 ms as one wave, 6.6 ms as two).
+//
 // Layout: instance q owns arena[base_q, base_q + n_q) of the packed arena (one
 // 64-bit word per vertex: value and the id of the round that last lowered it;
 // with IRGL_TUNE_NO_PACKED a state and a stamp arena instead) and the same
@@ -32,6 +38,11 @@ struct BQuery {
   uint32_t rounds = 0;
 };
 
+struct Wave {
+  uint32_t q0, q1;  // query ids [q0, q1)
+  uint64_t n;       // vertices
+};
+
 }  // namespace
 
 struct irgl_batch {
@@ -50,6 +61,12 @@ struct irgl_batch {
   uint32_t* items[2] = {nullptr, nullptr};
   uint32_t* qlast = nullptr;
   uint32_t* qlast_host = nullptr;
+  uint32_t* qfirst = nullptr;         // per query: the round id its wave started at
+  uint32_t* qfirst_host = nullptr;
+  uint64_t wave_bytes = 0;            // 0: half the L2
+  std::vector<Wave> waves;
+  std::vector<AdmitParams> aps;       // one admission per wave
+  uint32_t epoch_prev = 1;            // device epoch after the previous run
   uint32_t* cont = nullptr;
   uint32_t* srcs = nullptr;
   uint32_t* sbases = nullptr;
@@ -61,7 +78,6 @@ struct irgl_batch {
   irgl_tuning t{};
   uint32_t grid = 0;
   BParams bp{};
-  AdmitParams ap{};
   uint32_t admit_grid = 0;
   bool graph_ok = false;
   cudaGraph_t graph = nullptr;
@@ -115,6 +131,7 @@ void batch_free_device(irgl_batch* b) {
   cudaFree(b->items[0]);
   cudaFree(b->items[1]);
   cudaFree(b->qlast);
+  cudaFree(b->qfirst);
   cudaFree(b->cont);
   cudaFree(b->srcs);
   cudaFree(b->sbases);
@@ -126,6 +143,10 @@ void batch_free_device(irgl_batch* b) {
   b->big_off = nullptr;
   b->big_cap = 0;
   if (b->qlast_host) cudaFreeHost(b->qlast_host);
+  if (b->qfirst_host) cudaFreeHost(b->qfirst_host);
+  b->qfirst = b->qfirst_host = nullptr;
+  b->waves.clear();
+  b->aps.clear();
   b->state = b->stamp = b->items[0] = b->items[1] = b->qlast = b->cont = b->srcs = b->sbases = nullptr;
   b->ds = nullptr;
   b->qlast_host = nullptr;
@@ -139,15 +160,19 @@ void batch_reset_status(irgl_batch* b) {
   std::memset(&z, 0, sizeof(z));
   z.epoch = 1;
   *b->st_host = z;
+  b->epoch_prev = z.epoch;
   cudaMemcpyAsync(b->st, b->st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, b->stream);
   if (b->stamp) cudaMemsetAsync(b->stamp, 0, sizeof(uint32_t) * b->arena_n, b->stream);
   cudaStreamSynchronize(b->stream);
 }
 
 cudaError_t enqueue(irgl_batch* b) {
-  cudaError_t e = cudaMemsetAsync(b->cont, 0, 2 * sizeof(uint32_t), b->stream);
-  if (e == cudaSuccess) e = launch_admit(b->ap, b->admit_grid, b->stream);
-  if (e == cudaSuccess) e = launch_batch_iterate(b->t.cta_size, b->grid, b->bp, b->stream);
+  cudaError_t e = cudaSuccess;
+  for (const AdmitParams& ap : b->aps) {  // one wave after another
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->cont, 0, 2 * sizeof(uint32_t), b->stream);
+    if (e == cudaSuccess) e = launch_admit(ap, b->admit_grid, b->stream);
+    if (e == cudaSuccess) e = launch_batch_iterate(b->t.cta_size, b->grid, b->bp, b->stream);
+  }
   // results: the value halves of the packed words
   if (e == cudaSuccess && b->ds) e = launch_extract_values(b->ds, b->state, b->arena_n, b->admit_grid, b->stream);
   return e;
@@ -258,17 +283,34 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   }
   b->arena_n = std::max<uint64_t>(total, 1);
   const uint32_t Q = static_cast<uint32_t>(b->qs.size());
+  // waves: consecutive queries while their packed state fits the budget
+  uint64_t budget = b->wave_bytes;
+  if (budget == 0) {
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device);
+    budget = std::max<uint64_t>(static_cast<uint64_t>(l2) / 2, 1);
+  }
+  b->waves.clear();
+  for (uint32_t i = 0; i < Q; ++i) {
+    const uint64_t bytes = 8ull * b->qs[i].n;
+    if (b->waves.empty() || 8ull * b->waves.back().n + bytes > budget) b->waves.push_back(Wave{i, i, 0});
+    b->waves.back().q1 = i + 1;
+    b->waves.back().n += b->qs[i].n;
+  }
   std::vector<QDesc> desc(Q);
   std::vector<QNew> qn(Q);
   std::vector<uint32_t> bases(Q), flat;
   flat.reserve(nsrc);
-  for (uint32_t i = 0; i < Q; ++i) {
-    const BQuery& q = b->qs[i];
-    desc[i] = QDesc{q.g->row_ptr, q.g->col, q.g->w, q.n, q.op, q.base, i};
-    bases[i] = q.base;
-    qn[i] = QNew{q.base, q.n, q.op, i, static_cast<uint32_t>(flat.size()), static_cast<uint32_t>(q.srcs.size()),
-                 q.base, 0};
-    flat.insert(flat.end(), q.srcs.begin(), q.srcs.end());
+  for (const Wave& wv : b->waves) {
+    for (uint32_t i = wv.q0; i < wv.q1; ++i) {
+      const BQuery& q = b->qs[i];
+      desc[i] = QDesc{q.g->row_ptr, q.g->col, q.g->w, q.n, q.op, q.base, i};
+      bases[i] = q.base;
+      // pre: exclusive prefix of n within the wave (the admission kernels' index space)
+      qn[i] = QNew{q.base, q.n, q.op, i, static_cast<uint32_t>(flat.size()), static_cast<uint32_t>(q.srcs.size()),
+                   q.base - b->qs[wv.q0].base, 0};
+      flat.insert(flat.end(), q.srcs.begin(), q.srcs.end());
+    }
   }
   // packed (value, round id) words unless the two-array form is asked for; the
   // u32 state arena then holds the results, extracted after each run
@@ -282,6 +324,8 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   if (e == cudaSuccess) e = cudaMalloc(&b->items[1], sizeof(uint32_t) * b->arena_n);
   if (e == cudaSuccess) e = cudaMalloc(&b->qlast, sizeof(uint32_t) * Q);
   if (e == cudaSuccess) e = cudaMallocHost(&b->qlast_host, sizeof(uint32_t) * Q);
+  if (e == cudaSuccess) e = cudaMalloc(&b->qfirst, sizeof(uint32_t) * Q);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->qfirst_host, sizeof(uint32_t) * Q);
   if (e == cudaSuccess) e = cudaMalloc(&b->cont, 128);
   if (e == cudaSuccess) e = cudaMalloc(&b->srcs, sizeof(uint32_t) * std::max<size_t>(flat.size(), 1));
   if (e == cudaSuccess) e = cudaMalloc(&b->sbases, sizeof(uint32_t) * Q);
@@ -340,19 +384,24 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   b->bp.trace = ctx->trace;
   b->bp.trace_cap = ctx->trace_cap;
   b->bp.big = (t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{b->big_e, b->big_off, b->big_cap};
-  b->ap = AdmitParams{};
-  b->ap.qn = b->qnew;
-  b->ap.nnew = Q;
-  b->ap.total = static_cast<uint32_t>(total);
-  b->ap.srcs = b->srcs;
-  b->ap.state = b->state;
-  b->ap.ds = b->ds;
-  b->ap.qlast = b->qlast;
-  b->ap.items[0] = b->items[0];
-  b->ap.items[1] = b->items[1];
-  b->ap.cap = static_cast<uint32_t>(b->arena_n);
-  b->ap.cont = b->cont;
-  b->ap.st = b->st;
+  b->aps.clear();
+  for (const Wave& wv : b->waves) {
+    AdmitParams ap{};
+    ap.qn = b->qnew + wv.q0;
+    ap.nnew = wv.q1 - wv.q0;
+    ap.total = static_cast<uint32_t>(wv.n);
+    ap.srcs = b->srcs;
+    ap.state = b->state;
+    ap.ds = b->ds;
+    ap.qlast = b->qlast;
+    ap.qfirst = b->qfirst;
+    ap.items[0] = b->items[0];
+    ap.items[1] = b->items[1];
+    ap.cap = static_cast<uint32_t>(b->arena_n);
+    ap.cont = b->cont;
+    ap.st = b->st;
+    b->aps.push_back(ap);
+  }
   b->admit_grid = static_cast<uint32_t>(ctx->sm_count) * 4;
   b->graph_ok = false;
   if (use_cuda_graph) {
@@ -379,6 +428,18 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   return IRGL_OK;
 }
 
+irgl_status irgl_batch_set_wave_bytes(irgl_batch* b, uint64_t bytes) {
+  if (!b) return fail(IRGL_ERR_INVALID_ARG, "batch is NULL");
+  b->wave_bytes = bytes;
+  return IRGL_OK;
+}
+
+irgl_status irgl_batch_waves(irgl_batch* b, uint32_t* waves) {
+  if (!b || !waves) return fail(IRGL_ERR_INVALID_ARG, "NULL argument");
+  *waves = static_cast<uint32_t>(b->waves.size());
+  return IRGL_OK;
+}
+
 irgl_status irgl_batch_launch(irgl_batch* b) {
   if (!b || !b->prepared) return fail(IRGL_ERR_INVALID_ARG, "batch not prepared");
   DeviceGuard guard(b->ctx->device);
@@ -396,16 +457,19 @@ irgl_status irgl_batch_sync(irgl_batch* b, irgl_stats* stats) {
   cudaError_t e = cudaMemcpyAsync(b->st_host, b->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->qlast_host, b->qlast, sizeof(uint32_t) * Q, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->qfirst_host, b->qfirst, sizeof(uint32_t) * Q, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(e, "batch sync");
   const DevStatus st = *b->st_host;
-  b->ctx->st_host->rounds = st.rounds;  // lets irgl_trace_read size a batch trace
+  b->ctx->st_host->rounds = st.rounds;  // lets irgl_trace_read size a batch trace (the last wave's)
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
-    stats->rounds = st.rounds;
+    stats->rounds = st.epoch - b->epoch_prev;  // every wave's rounds
     stats->grid = b->grid;
     stats->cta_size = b->t.cta_size;
-    stats->launches = 3;
+    // per wave: fill, sources, iterate; then the result extraction
+    stats->launches = 3u * static_cast<uint32_t>(b->waves.size()) + (b->ds ? 1u : 0u);
     stats->edges_scanned = st.edges;
     stats->last_out = st.last_out;
     float ms = 0.f;
@@ -423,9 +487,9 @@ irgl_status irgl_batch_sync(irgl_batch* b, irgl_stats* stats) {
     batch_reset_status(b);
     return s;
   }
-  // per-instance rounds from the termination flags
-  const uint32_t ep0 = st.epoch - st.rounds;  // round id of this run's first round
-  for (uint32_t i = 0; i < Q; ++i) b->qs[i].rounds = b->qlast_host[i] - ep0 + 2;
+  // per-instance rounds from the termination flags and the round its wave began at
+  for (uint32_t i = 0; i < Q; ++i) b->qs[i].rounds = b->qlast_host[i] - b->qfirst_host[i] + 2;
+  b->epoch_prev = st.epoch;
   cudaMemsetAsync(&b->st->edges, 0, sizeof(unsigned long long), b->stream);
   if (st.epoch > 0xF0000000u) batch_reset_status(b);
   return IRGL_OK;
@@ -487,6 +551,17 @@ irgl_status irgl_batch_copy_result(irgl_batch* b, uint32_t query_id, uint32_t* h
                                   cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(e, "batch result copy");
+  return IRGL_OK;
+}
+
+irgl_status irgl_batch_copy_results(irgl_batch* b, uint32_t* host_out) {
+  if (!b || !b->prepared || !host_out) return fail(IRGL_ERR_INVALID_ARG, "NULL argument or batch not prepared");
+  DeviceGuard guard(b->ctx->device);
+  uint64_t total = 0;
+  for (const BQuery& q : b->qs) total += q.n;  // bases are the running sums of n
+  cudaError_t e = cudaMemcpyAsync(host_out, b->state, sizeof(uint32_t) * total, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch results copy");
   return IRGL_OK;
 }
 

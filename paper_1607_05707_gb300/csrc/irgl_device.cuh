@@ -1945,6 +1945,7 @@ struct AdmitParams {
   uint32_t* state;
   unsigned long long* ds; // packed arena (when set, the initial values go here)
   uint32_t* qlast;
+  uint32_t* qfirst;       // optional, per query id: the round id it was admitted at
   uint32_t* items[2];
   uint32_t cap;
   uint32_t* cont;
@@ -2005,7 +2006,10 @@ __device__ __forceinline__ void admit_sources(const AdmitParams& a) {
   const uint32_t nthreads = gridDim.x * blockDim.x;
   uint32_t* buf = (__ldcg(a.cont) & 1u) ? a.items[1] : a.items[0];
   const uint32_t ep = __ldcg(&a.st->epoch);
-  for (uint32_t j = tid; j < a.nnew; j += nthreads) a.qlast[a.qn[j].slot] = ep - 1u;
+  for (uint32_t j = tid; j < a.nnew; j += nthreads) {
+    a.qlast[a.qn[j].slot] = ep - 1u;
+    if (a.qfirst != nullptr) a.qfirst[a.qn[j].slot] = ep;
+  }
   // one warp per new query walks its sources
   const uint32_t warp = tid >> 5, nwarps = nthreads >> 5, lane = threadIdx.x & 31;
   for (uint32_t j = warp; j < a.nnew; j += nwarps) {

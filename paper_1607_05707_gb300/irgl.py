@@ -195,12 +195,15 @@ _SIGS = {
     "irgl_batch_destroy": [_P],
     "irgl_batch_add": [_P, _P, c_int, _P, c_uint32, POINTER(c_uint32)],
     "irgl_batch_prepare": [_P, POINTER(irgl_tuning), c_int],
+    "irgl_batch_set_wave_bytes": [_P, c_uint64],
+    "irgl_batch_waves": [_P, POINTER(c_uint32)],
     "irgl_batch_launch": [_P],
     "irgl_batch_sync": [_P, POINTER(irgl_stats)],
     "irgl_batch_run": [_P, POINTER(irgl_stats)],
     "irgl_batch_info": [_P, POINTER(c_uint32), POINTER(c_uint32), POINTER(c_uint32), POINTER(c_int), POINTER(c_uint64)],
     "irgl_batch_result": [_P, c_uint32, POINTER(_P), POINTER(c_uint32), POINTER(c_uint32)],
     "irgl_batch_copy_result": [_P, c_uint32, _P],
+    "irgl_batch_copy_results": [_P, _P],
     "irgl_msf": [_P, _P, c_int, c_int, _P, c_uint32, c_int, POINTER(irgl_tuning), POINTER(irgl_msf_stats)],
 }
 _RESTYPE = {"irgl_last_error": c_char_p, "irgl_status_string": c_char_p}
@@ -399,6 +402,16 @@ def irgl_batch_prepare(b: int, tuning=None, use_cuda_graph: int = 1) -> None:
     _check(lib().irgl_batch_prepare(b, _tuning(tuning), use_cuda_graph))
 
 
+def irgl_batch_set_wave_bytes(b: int, nbytes: int) -> None:
+    _check(lib().irgl_batch_set_wave_bytes(b, nbytes))
+
+
+def irgl_batch_waves(b: int) -> int:
+    w = c_uint32()
+    _check(lib().irgl_batch_waves(b, ctypes.byref(w)))
+    return int(w.value)
+
+
 def irgl_batch_launch(b: int) -> None:
     _check(lib().irgl_batch_launch(b))
 
@@ -421,7 +434,7 @@ def irgl_batch_info(b: int) -> dict:
     _check(lib().irgl_batch_info(b, ctypes.byref(nq), ctypes.byref(grid), ctypes.byref(cta), ctypes.byref(cap),
                                  ctypes.byref(arena)))
     return dict(nqueries=int(nq.value), grid=int(grid.value), cta_size=int(cta.value),
-                graph_captured=bool(cap.value), arena_entries=int(arena.value))
+                graph_captured=bool(cap.value), arena_entries=int(arena.value), waves=irgl_batch_waves(b))
 
 
 def irgl_batch_result(b: int, query_id: int) -> tuple[int, int, int]:
@@ -432,6 +445,10 @@ def irgl_batch_result(b: int, query_id: int) -> tuple[int, int, int]:
 
 def irgl_batch_copy_result(b: int, query_id: int, host_out: int) -> None:
     _check(lib().irgl_batch_copy_result(b, query_id, host_out))
+
+
+def irgl_batch_copy_results(b: int, host_out: int) -> None:
+    _check(lib().irgl_batch_copy_results(b, host_out))
 
 
 def irgl_trace_enable(ctx: int, max_rounds: int) -> None:

@@ -68,6 +68,72 @@ def test_batch_matches_oracle(ctx, use_graph, tuning):
         dg.close()
 
 
+def _waves(sizes, budget):
+    # consecutive queries while their 8-byte packed words fit the budget
+    w, acc = 0, None
+    for n in sizes:
+        if acc is None or acc + 8 * n > budget:
+            w, acc = w + 1, 0
+        acc += 8 * n
+    return w
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("wave_bytes", [1, 8 * 3000, 8 * 20000, (1 << 64) - 1])
+def test_batch_waves_match_oracle(ctx, use_graph, wave_bytes):
+    """Queries split into consecutive waves (one persistent launch each) give the
+    same results, and each query's rounds still count its own rounds."""
+    from paper_1607_05707_gb300.api import Batch
+
+    inst = _instances()
+    graphs = [ctx.load(g) for _, g, _ in inst]
+    b = Batch(ctx, 64)
+    for (k, g, s), dg in zip(inst, graphs):
+        b.add(k, dg, s)
+    info = b.prepare(None, use_cuda_graph=use_graph, wave_bytes=wave_bytes)
+    waves = _waves([g.n for _, g, _ in inst], wave_bytes)
+    assert info["waves"] == waves
+    if wave_bytes == 1:
+        assert waves == len(inst)
+    for rep in range(2):
+        st = b.run()
+        assert st["launches"] == 3 * waves + 1
+        total = 0
+        for q, (k, g, s) in enumerate(inst):
+            got, rounds = b.result(q)
+            want = oracle.run(k, g, s)
+            np.testing.assert_array_equal(got, want, err_msg=f"query {q} ({k}) rep {rep} waves {waves}")
+            if k == "bfs":
+                assert rounds == int(want[want != INF].max()) + 1
+            total = max(total, rounds)
+        assert st["rounds"] >= total
+    b.close()
+    for dg in graphs:
+        dg.close()
+
+
+def test_batch_results_one_copy(ctx):
+    from paper_1607_05707_gb300.api import Batch
+
+    inst = _instances()[:10]
+    graphs = [ctx.load(g) for _, g, _ in inst]
+    b = Batch(ctx, 16)
+    for (k, g, s), dg in zip(inst, graphs):
+        b.add(k, dg, s)
+    b.prepare(wave_bytes=8 * 4000)
+    b.run()
+    res = b.results()
+    assert len(res) == len(inst)
+    for q, (k, g, s) in enumerate(inst):
+        np.testing.assert_array_equal(res[q], oracle.run(k, g, s), err_msg=f"query {q}")
+        np.testing.assert_array_equal(res[q], b.result(q)[0])
+    with pytest.raises(ValueError):
+        b.results(np.empty(3, dtype=np.uint32))
+    b.close()
+    for dg in graphs:
+        dg.close()
+
+
 def test_batch_alone_equals_mix(ctx):
     from paper_1607_05707_gb300.api import Batch, as_u32
 
