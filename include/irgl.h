@@ -320,8 +320,10 @@ irgl_status irgl_batch_copy_result(irgl_batch* b, uint32_t query_id, uint32_t* h
 irgl_status irgl_batch_copy_results(irgl_batch* b, uint32_t* host_out);
 /* Autotune a prepared batch: the same coordinate descent, each candidate timed
  * as the median event time of `reps` whole-batch runs (the batch is re-prepared
- * per candidate, with the CUDA-graph choice it was prepared with). The batch is
- * left prepared with the best tuning. */
+ * per candidate, with the CUDA-graph choice it was prepared with), then the
+ * wave budget (a quarter, half or all of the L2, or one wave; see
+ * irgl_batch_set_wave_bytes). The batch is left prepared with the best tuning
+ * and budget (irgl_batch_waves tells the wave count). */
 irgl_status irgl_batch_autotune(irgl_batch* b, uint32_t reps, irgl_tuning* best, float* best_ms);
 
 /* ---------------------------------------------------------------- serving

@@ -517,8 +517,26 @@ irgl_status irgl_batch_autotune(irgl_batch* b, uint32_t reps, irgl_tuning* best,
     return ms[ms.size() / 2];
   };
   irgl_status s = tune_descend(measure, best, best_ms);
-  if (s == IRGL_OK) s = irgl_batch_prepare(b, best, use_graph);
-  return s;
+  if (s != IRGL_OK) return s;
+  // then the wave budget: a quarter, half (the default) and all of the L2, and one wave
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->ctx->device);
+  const uint64_t keep = b->wave_bytes;
+  uint64_t best_w = keep;
+  float w_ms = best_ms ? *best_ms : measure(*best);
+  const uint64_t l2b = static_cast<uint64_t>(l2);
+  const uint64_t budgets[4] = {l2b / 4, l2b / 2, l2b, ~uint64_t{0}};
+  for (uint64_t w : budgets) {
+    b->wave_bytes = w;
+    const float ms = measure(*best);
+    if (ms >= 0 && ms < w_ms * 0.98f) {
+      w_ms = ms;
+      best_w = w;
+    }
+  }
+  b->wave_bytes = best_w;
+  if (best_ms) *best_ms = w_ms;
+  return irgl_batch_prepare(b, best, use_graph);
 }
 
 irgl_status irgl_batch_info(irgl_batch* b, uint32_t* nqueries, uint32_t* grid, uint32_t* cta_size,

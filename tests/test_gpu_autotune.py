@@ -70,6 +70,9 @@ def test_autotune_batch(ctx):
     t, ms = b.autotune(reps=2)
     _valid(t)
     assert ms > 0
+    from paper_1607_05707_gb300 import irgl as C
+
+    assert C.irgl_batch_info(b.handle)["waves"] >= 1  # left prepared with the chosen wave budget
     b.run()
     for q, kind, g, s in qs:
         got, _ = b.result(q)
