@@ -296,10 +296,15 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* t, int use_cuda
  * whose packed state (8 bytes per vertex) fits in `bytes`; a run admits and
  * iterates one group after another (one persistent launch each, all in the
  * same CUDA graph), so the random state accesses of the active group hit L2
- * instead of DRAM. 0 (the default) = half the device's L2; UINT64_MAX = one
- * wave (every query active at once). A query larger than `bytes` is a wave of
- * its own. Takes effect at the next irgl_batch_prepare. The per-query rounds
- * count the rounds of the query's own wave; stats->rounds sums the waves. */
+ * instead of DRAM. This pays for low-diameter queries whose rounds are
+ * bandwidth-bound (256 R-MAT instances: 8.5 -> 6.6 ms with L2 / 2) and costs
+ * for high-diameter ones, whose rounds are latency-bound and which then run
+ * their rounds wave after wave (64 BFS on a 1024^2 grid: 10 waves, 10x the
+ * rounds); irgl_batch_autotune measures the choice. 0 (the default) or
+ * UINT64_MAX = one wave (every query active at once). A query larger than
+ * `bytes` is a wave of its own. Takes effect at the next irgl_batch_prepare.
+ * The per-query rounds count the rounds of the query's own wave;
+ * stats->rounds sums the waves. */
 irgl_status irgl_batch_set_wave_bytes(irgl_batch* b, uint64_t bytes);
 irgl_status irgl_batch_waves(irgl_batch* b, uint32_t* waves);
 /* Enqueue one run (events bracket it); irgl_batch_sync waits, checks the device

@@ -199,7 +199,7 @@ class Batch:
         return q
 
     def prepare(self, tuning=None, use_cuda_graph: bool = True, wave_bytes: int | None = None) -> dict:
-        """wave_bytes: packed-state budget of one wave (0 = half the L2, 2**64 - 1 = one wave)."""
+        """wave_bytes: packed-state budget of one wave (0 or 2**64 - 1 = one wave, the default)."""
         if wave_bytes is not None:
             C.irgl_batch_set_wave_bytes(self.handle, wave_bytes)
         C.irgl_batch_prepare(self.handle, tuning, 1 if use_cuda_graph else 0)

@@ -1,11 +1,12 @@
 // Batching: many independent queries (instances) in one persistent cooperative
 // launch, captured once in a CUDA graph and replayed.
 //
-// Waves: the queries are split, in add order, into consecutive groups whose
-// packed state fits in a byte budget (default half the L2); a run admits and
-// iterates one group after another, each one persistent launch, so the random
-// state accesses of the active group stay in L2 (256 R-MAT instances of 16.4 M
-// vertices in all: 8.4 ms as one wave, 6.6 ms as two).
+// Waves (optional; the autotuner measures them): the queries are split, in add
+// order, into consecutive groups whose packed state fits in a byte budget; a
+// run admits and iterates one group after another, each one persistent launch,
+// so the random state accesses of the active group stay in L2 (256 R-MAT
+// instances of 16.4 M vertices in all: 8.4 ms as one wave, 6.6 ms as two with
+// half the L2 each). High-diameter queries lose: their rounds repeat per wave.
 //
 // Layout: instance q owns arena[base_q, base_q + n_q) of the packed arena (one
 // 64-bit word per vertex: value and the id of the round that last lowered it;
@@ -63,7 +64,7 @@ struct irgl_batch {
   uint32_t* qlast_host = nullptr;
   uint32_t* qfirst = nullptr;         // per query: the round id its wave started at
   uint32_t* qfirst_host = nullptr;
-  uint64_t wave_bytes = 0;            // 0: half the L2
+  uint64_t wave_bytes = 0;            // 0: one wave
   std::vector<Wave> waves;
   std::vector<AdmitParams> aps;       // one admission per wave
   uint32_t epoch_prev = 1;            // device epoch after the previous run
@@ -284,12 +285,7 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   b->arena_n = std::max<uint64_t>(total, 1);
   const uint32_t Q = static_cast<uint32_t>(b->qs.size());
   // waves: consecutive queries while their packed state fits the budget
-  uint64_t budget = b->wave_bytes;
-  if (budget == 0) {
-    int l2 = 0;
-    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device);
-    budget = std::max<uint64_t>(static_cast<uint64_t>(l2) / 2, 1);
-  }
+  const uint64_t budget = b->wave_bytes == 0 ? ~uint64_t{0} : b->wave_bytes;  // 0: one wave
   b->waves.clear();
   for (uint32_t i = 0; i < Q; ++i) {
     const uint64_t bytes = 8ull * b->qs[i].n;

@@ -79,7 +79,7 @@ def _waves(sizes, budget):
 
 
 @pytest.mark.parametrize("use_graph", [True, False])
-@pytest.mark.parametrize("wave_bytes", [1, 8 * 3000, 8 * 20000, (1 << 64) - 1])
+@pytest.mark.parametrize("wave_bytes", [1, 8 * 3000, 8 * 20000, 0, (1 << 64) - 1])
 def test_batch_waves_match_oracle(ctx, use_graph, wave_bytes):
     """Queries split into consecutive waves (one persistent launch each) give the
     same results, and each query's rounds still count its own rounds."""
@@ -91,7 +91,7 @@ def test_batch_waves_match_oracle(ctx, use_graph, wave_bytes):
     for (k, g, s), dg in zip(inst, graphs):
         b.add(k, dg, s)
     info = b.prepare(None, use_cuda_graph=use_graph, wave_bytes=wave_bytes)
-    waves = _waves([g.n for _, g, _ in inst], wave_bytes)
+    waves = _waves([g.n for _, g, _ in inst], wave_bytes or (1 << 64) - 1)  # 0: one wave
     assert info["waves"] == waves
     if wave_bytes == 1:
         assert waves == len(inst)
