@@ -93,7 +93,8 @@ typedef struct {
                              value (distance, label) >= the current limit wait on a far list until
                              the rounds below the limit drain; 0 = plain rounds (every improvement
                              is pushed). CC with delta = 1 floods the smallest label first, so
-                             each vertex mostly takes its final label once */
+                             each vertex mostly takes its final label once. Batches and servers:
+                             per-query near-far for their SSSP queries (below) */
 } irgl_tuning;
 
 #define IRGL_TUNE_NO_SPLIT 0x1u
@@ -280,13 +281,22 @@ irgl_status irgl_autotune(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uin
  * as the preference. irgl_batch_prepare allocates the arena (20 bytes per
  * instance vertex: a 64-bit word holding the value and the id of the round
  * that last lowered it, the u32 result and two worklist entries; 16 bytes with
- * IRGL_TUNE_NO_PACKED, which keeps values and stamps in two arrays), uploads
+ * IRGL_TUNE_NO_PACKED, which keeps values and stamps in two arrays; 32 bytes
+ * with near-far), uploads
  * the descriptors and, with use_cuda_graph = 1, captures the whole launch
  * sequence (admission kernels + persistent kernel + result extraction) in a
  * CUDA graph that irgl_batch_launch replays (if the
  * capture fails the sequence is launched directly; irgl_batch_info tells).
  * Every launch recomputes all instances from their sources.
- * Queries are added before prepare; query ids are 0, 1, ... in add order. */
+ * Queries are added before prepare; query ids are 0, 1, ... in add order.
+ * Near-far (tuning delta != 0, packed words): each SSSP query has its own
+ * limit, delta at admission. A popped item whose distance is at or above its
+ * query's limit is not expanded; it waits on a far list, which every round
+ * looks at once: items its query's limit has passed go back onto the
+ * out-worklist, the rest stay. A query's limit rises by delta after every
+ * round in which it pushed nothing onto the out-worklist. Results are the
+ * same; only the edges scanned and the rounds change (64 SSSP queries on a
+ * 1024^2 weighted mesh scan about 40 times its edges each with plain rounds). */
 irgl_status irgl_batch_create(irgl_ctx* ctx, uint32_t max_queries /* <= 1024 */, irgl_batch** out);
 irgl_status irgl_batch_destroy(irgl_batch* b);
 irgl_status irgl_batch_add(irgl_batch* b, irgl_graph* g, irgl_kernel k, const uint32_t* srcs_host, uint32_t nsrc,
@@ -325,8 +335,8 @@ irgl_status irgl_batch_copy_result(irgl_batch* b, uint32_t query_id, uint32_t* h
 irgl_status irgl_batch_copy_results(irgl_batch* b, uint32_t* host_out);
 /* Autotune a prepared batch: the same coordinate descent, each candidate timed
  * as the median event time of `reps` whole-batch runs (the batch is re-prepared
- * per candidate, with the CUDA-graph choice it was prepared with), then the
- * wave budget (a quarter, half or all of the L2, or one wave; see
+ * per candidate, with the CUDA-graph choice it was prepared with; the
+ * near-far delta too when the batch holds SSSP queries), then the wave budget (a quarter, half or all of the L2, or one wave; see
  * irgl_batch_set_wave_bytes). The batch is left prepared with the best tuning
  * and budget (irgl_batch_waves tells the wave count). */
 irgl_status irgl_batch_autotune(irgl_batch* b, uint32_t reps, irgl_tuning* best, float* best_ms);
@@ -335,7 +345,8 @@ irgl_status irgl_batch_autotune(irgl_batch* b, uint32_t reps, irgl_tuning* best,
  * Continuous batching server for BFS/SSSP queries against device-resident
  * graphs. A worker thread admits queued queries in arrival order while a
  * slot is free and the query's state fits the device arena (20 bytes per
- * vertex of its graph, 16 with IRGL_TUNE_NO_PACKED; first-fit), launches
+ * vertex of its graph, 16 with IRGL_TUNE_NO_PACKED, 32 with near-far as in
+ * batches (tuning delta); first-fit), launches
  * epochs of the batched persistent
  * kernel (at most epoch_rounds rounds over every active query), and retires
  * the queries that finished: their result is copied to the caller's host

@@ -63,6 +63,9 @@ struct irgl_batch {
   uint32_t* qlast = nullptr;
   uint32_t* qlast_host = nullptr;
   uint32_t* qfirst = nullptr;         // per query: the round id its wave started at
+  uint32_t* far_items[2] = {nullptr, nullptr};  // near-far (tuning delta != 0): far lists
+  uint32_t* far_stamp = nullptr;      //   arena: round id of the far list a vertex was last put on
+  uint32_t* blim = nullptr;           //   per query: its limit
   uint32_t* qfirst_host = nullptr;
   uint64_t wave_bytes = 0;            // 0: one wave
   std::vector<Wave> waves;
@@ -133,6 +136,11 @@ void batch_free_device(irgl_batch* b) {
   cudaFree(b->items[1]);
   cudaFree(b->qlast);
   cudaFree(b->qfirst);
+  cudaFree(b->far_items[0]);
+  cudaFree(b->far_items[1]);
+  cudaFree(b->far_stamp);
+  cudaFree(b->blim);
+  b->far_items[0] = b->far_items[1] = b->far_stamp = b->blim = nullptr;
   cudaFree(b->cont);
   cudaFree(b->srcs);
   cudaFree(b->sbases);
@@ -164,13 +172,14 @@ void batch_reset_status(irgl_batch* b) {
   b->epoch_prev = z.epoch;
   cudaMemcpyAsync(b->st, b->st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, b->stream);
   if (b->stamp) cudaMemsetAsync(b->stamp, 0, sizeof(uint32_t) * b->arena_n, b->stream);
+  if (b->far_stamp) cudaMemsetAsync(b->far_stamp, 0, sizeof(uint32_t) * b->arena_n, b->stream);
   cudaStreamSynchronize(b->stream);
 }
 
 cudaError_t enqueue(irgl_batch* b) {
   cudaError_t e = cudaSuccess;
   for (const AdmitParams& ap : b->aps) {  // one wave after another
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->cont, 0, 2 * sizeof(uint32_t), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->cont, 0, 4 * sizeof(uint32_t), b->stream);
     if (e == cudaSuccess) e = launch_admit(ap, b->admit_grid, b->stream);
     if (e == cudaSuccess) e = launch_batch_iterate(b->t.cta_size, b->grid, b->bp, b->stream);
   }
@@ -321,6 +330,12 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   if (e == cudaSuccess) e = cudaMalloc(&b->qlast, sizeof(uint32_t) * Q);
   if (e == cudaSuccess) e = cudaMallocHost(&b->qlast_host, sizeof(uint32_t) * Q);
   if (e == cudaSuccess) e = cudaMalloc(&b->qfirst, sizeof(uint32_t) * Q);
+  // near-far for the SSSP queries (packed words only): two far lists, a far stamp per vertex
+  const bool nf = t.delta != 0 && packed;
+  if (nf && e == cudaSuccess) e = cudaMalloc(&b->far_items[0], sizeof(uint32_t) * b->arena_n);
+  if (nf && e == cudaSuccess) e = cudaMalloc(&b->far_items[1], sizeof(uint32_t) * b->arena_n);
+  if (nf && e == cudaSuccess) e = cudaMalloc(&b->far_stamp, sizeof(uint32_t) * b->arena_n);
+  if (nf && e == cudaSuccess) e = cudaMalloc(&b->blim, sizeof(uint32_t) * Q);
   if (e == cudaSuccess) e = cudaMallocHost(&b->qfirst_host, sizeof(uint32_t) * Q);
   if (e == cudaSuccess) e = cudaMalloc(&b->cont, 128);
   if (e == cudaSuccess) e = cudaMalloc(&b->srcs, sizeof(uint32_t) * std::max<size_t>(flat.size(), 1));
@@ -336,6 +351,7 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
     return cuda_fail(e, "batch arena allocation");
   }
   if (b->stamp) e = cudaMemsetAsync(b->stamp, 0, sizeof(uint32_t) * b->arena_n, b->stream);
+  if (e == cudaSuccess && b->far_stamp) e = cudaMemsetAsync(b->far_stamp, 0, sizeof(uint32_t) * b->arena_n, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->cont, 0, 128, b->stream);
   if (e == cudaSuccess && !flat.empty())
     e = cudaMemcpyAsync(b->srcs, flat.data(), sizeof(uint32_t) * flat.size(), cudaMemcpyHostToDevice, b->stream);
@@ -380,6 +396,12 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   b->bp.trace = ctx->trace;
   b->bp.trace_cap = ctx->trace_cap;
   b->bp.big = (t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{b->big_e, b->big_off, b->big_cap};
+  b->bp.delta = nf ? t.delta : 0u;
+  b->bp.blim = b->blim;
+  b->bp.far_items[0] = b->far_items[0];
+  b->bp.far_items[1] = b->far_items[1];
+  b->bp.far_cap = nf ? static_cast<uint32_t>(b->arena_n) : 0u;
+  b->bp.far_stamp = b->far_stamp;
   b->aps.clear();
   for (const Wave& wv : b->waves) {
     AdmitParams ap{};
@@ -391,6 +413,8 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
     ap.ds = b->ds;
     ap.qlast = b->qlast;
     ap.qfirst = b->qfirst;
+    ap.blim = b->blim;
+    ap.delta = b->bp.delta;
     ap.items[0] = b->items[0];
     ap.items[1] = b->items[1];
     ap.cap = static_cast<uint32_t>(b->arena_n);
@@ -512,7 +536,9 @@ irgl_status irgl_batch_autotune(irgl_batch* b, uint32_t reps, irgl_tuning* best,
     std::sort(ms.begin(), ms.end());
     return ms[ms.size() / 2];
   };
-  irgl_status s = tune_descend(measure, best, best_ms);
+  bool has_sssp = false;  // near-far delta is searched when the batch holds SSSP queries
+  for (const BQuery& q : b->qs) has_sssp |= q.op == IRGL_SSSP;
+  irgl_status s = tune_descend(measure, best, best_ms, has_sssp);
   if (s != IRGL_OK) return s;
   // then the wave budget: a quarter, half (the default) and all of the L2, and one wave
   int l2 = 0;

@@ -60,7 +60,7 @@ enum : uint32_t {
 };
 
 // Device status block. Each contended family sits on its own 128-byte line.
-// Invariant between launches: arrive, exit_count, tail[], grab[], rel, qmask,
+// Invariant between launches: arrive, exit_count, tail[], grab[], rel, qmask, qnear, bfar_tail,
 // big_ctr, any_true and any_false are 0 (every kernel restores them on a
 // clean exit; the host clears the block after an error).
 constexpr uint32_t kMaxGrid = 2048;  // CTAs of a persistent launch (16-bit arrival count)
@@ -102,8 +102,13 @@ struct alignas(128) DevStatus {
   // direction-optimising BFS: out-edges of the vertices each round pushed (triple-buffered)
   unsigned long long mf[3];
   uint32_t pad7[18];
+  // batched near-far: per-round bitmaps of the queries (by slot) that pushed to
+  // the out-worklist, and the sizes of the far lists (both triple-buffered)
+  uint32_t qnear[3][32];
+  uint32_t bfar_tail[3];
+  uint32_t pad8[29];
 };
-static_assert(sizeof(DevStatus) == 1152, "status layout");
+static_assert(sizeof(DevStatus) == 1664, "status layout");
 
 // Long adjacency lists of a round (degree >= cta_thresh) are not walked by the
 // CTA that popped them: they go to a grid-wide list and, after a barrier, every
@@ -221,6 +226,14 @@ struct BParams {
   unsigned long long* trace;
   uint32_t trace_cap;
   BigList big;
+  // near-far for SSSP queries (delta != 0): a popped item at or above its
+  // query's limit waits on the far list; cont[2], cont[3] carry the far list
+  // (buffer, size) between launches like cont[0], cont[1] the out-worklist
+  uint32_t delta;
+  uint32_t* blim;           // per slot: the query's limit at the end of the last launch
+  uint32_t* far_items[2];   // far lists of arena indices
+  uint32_t far_cap;
+  uint32_t* far_stamp;      // arena: round id of the far list a vertex was last put on
 };
 
 // ----------------------------------------------------------------------------- small helpers
@@ -326,7 +339,9 @@ template <int CTA>
 struct BatchSmem {
   Smem<CTA> core;
   uint32_t sbases[kMaxBatchQueries];
-  uint32_t qbits[kMaxBatchQueries / 32];  // queries (by id) this CTA pushed for in the current round
+  uint32_t qbits[kMaxBatchQueries / 32];  // queries (by slot) this CTA pushed for in the current round
+  uint32_t qfar[kMaxBatchQueries / 32];   // queries (by slot) this CTA kept on the far list
+  uint32_t lim[kMaxBatchQueries];         // near-far: this round's limit of each query (by id)
 };
 
 // ----------------------------------------------------------------------------- cooperative-conversion push
@@ -491,6 +506,7 @@ struct SingleView {
   uint32_t* stamp;
   uint32_t n;
   static constexpr bool kBatched = false;
+  static constexpr const uint32_t* lim = nullptr;
   __device__ __forceinline__ uint32_t nverts(uint32_t) const { return n; }
   __device__ __forceinline__ uint32_t op(uint32_t) const { return OP; }
   __device__ __forceinline__ const uint32_t* rowp(uint32_t) const { return row_ptr; }
@@ -509,6 +525,9 @@ struct BatchView {
   uint32_t* state;
   uint32_t* stamp;
   uint32_t* qbits;  // shared-memory bitmap of queries that pushed this round
+  uint32_t* qfar;   // shared-memory bitmap of queries that kept far items this round
+  const uint32_t* lim;  // near-far: per-query limits (shared memory), or nullptr
+  uint32_t* far_stamp;
   static constexpr bool kBatched = true;
   __device__ __forceinline__ uint32_t op(uint32_t q) const { return __ldg(&desc[q].op); }
   __device__ __forceinline__ const uint32_t* rowp(uint32_t q) const {
@@ -537,6 +556,11 @@ struct BatchView {
   __device__ __forceinline__ void mark(uint32_t q, uint32_t) const {
     const uint32_t slot = __ldg(&desc[q].slot);
     atomicOr(&qbits[slot >> 5], 1u << (slot & 31u));
+  }
+  // near-far: the query holds far items (still active, but no out-worklist push)
+  __device__ __forceinline__ void mark_far(uint32_t q) const {
+    const uint32_t slot = __ldg(&desc[q].slot);
+    atomicOr(&qfar[slot >> 5], 1u << (slot & 31u));
   }
 };
 
@@ -608,6 +632,8 @@ struct RoundCtx {
   uint32_t dsr;                   //   and this round's id in them (1, 2, ...)
   uint32_t local_rounds;          // CTA-local sub-rounds after the tiles (0 = none)
   const uint32_t* local_items;    // a sub-round's items: a range of the CTA's stage (shared memory)
+  const uint32_t* far_in;         // batched near-far: the far items waiting from earlier rounds
+  uint32_t far_in_n;
 };
 
 // The destination's current value as the operator reads it. BFS with the
@@ -863,6 +889,61 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
 }
 
 
+// Batched near-far: put `item` of query q on this round's far list (want; at
+// most once per round by the far stamp) and mark the query as still active.
+// Called by every lane of a converged warp.
+template <int CTA, class V>
+__device__ __forceinline__ void push_far_item(const V& g, Smem<CTA>& sm, const RoundCtx& rc, bool want, uint32_t item,
+                                              uint32_t q) {
+  bool f = false;
+  if (want) {
+    f = atomicExch(g.far_stamp + item, rc.ep) != rc.ep;
+    g.mark_far(q);
+  }
+  push_far4<CTA>(sm, rc.far_out, f ? 1u : 0u, item, 0u, 0u, 0u, kInf);
+}
+
+// Put the round id `dsr` into a packed (value, round id) word whose value it
+// keeps: true when this call did it (the caller pushes the vertex), false when
+// the word already holds dsr (the vertex is already on this round's
+// out-worklist). A bounded CAS loop; a word lowered under it is re-read.
+__device__ __forceinline__ bool stamp_pending(unsigned long long* p, unsigned long long w, uint32_t dsr) {
+  for (int k = 0; k < 64; ++k) {
+    if (static_cast<uint32_t>(w) == dsr) return false;
+    const unsigned long long o = atomicCAS(p, w, (w & 0xFFFFFFFF00000000ull) | dsr);
+    if (o == w) return true;
+    w = o;
+  }
+  return true;  // contended: push anyway (a duplicate only repeats an expansion)
+}
+
+// Batched near-far: every far item of the last round is looked at once. Its
+// query's limit has passed it: it goes onto this round's out-worklist (a near
+// push, so the limit stays); else it stays on the far list. Static share per
+// CTA; the trip count is CTA-uniform, so the warp-aggregated pushes converge.
+template <int CTA, class V>
+__device__ __forceinline__ void far_sweep(const V& g, Smem<CTA>& sm, const RoundCtx& rc) {
+  for (uint32_t base = blockIdx.x * CTA; base < rc.far_in_n; base += gridDim.x * CTA) {
+    const uint32_t i = base + threadIdx.x;
+    bool near = false, keep = false;
+    uint32_t item = 0, q = 0;
+    if (i < rc.far_in_n) {
+      item = __ldcg(rc.far_in + i);
+      uint32_t u;
+      g.decode(item, q, u);
+      const unsigned long long w = __ldcg(rc.ds + item);
+      if (static_cast<uint32_t>(w >> 32) < g.lim[q]) {
+        near = stamp_pending(rc.ds + item, w, rc.dsr);
+        if (near) g.mark(q, rc.ep);
+      } else {
+        keep = true;
+      }
+    }
+    push1<CTA>(sm, rc.out, near, item);
+    push_far_item<CTA>(g, sm, rc, keep, item, q);
+  }
+}
+
 template <uint32_t OP, int CTA, int RED, class V>
 __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const RoundCtx& rc, uint32_t idx,
                                              uint32_t& edges, uint32_t& any_true, uint32_t& any_false) {
@@ -870,9 +951,9 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
   const uint32_t lane = tid & 31;
   const uint32_t wbase = tid & ~31u;
   bool valid = idx < rc.in_n;
-  uint32_t q = 0, beg = 0, end = 0, val = 0;
+  uint32_t q = 0, beg = 0, end = 0, val = 0, item = 0;
   if (valid) {
-    const uint32_t item = rc.local_items ? rc.local_items[idx] : (rc.in_items ? __ldcg(rc.in_items + idx) : idx);
+    item = rc.local_items ? rc.local_items[idx] : (rc.in_items ? __ldcg(rc.in_items + idx) : idx);
     uint32_t u;
     g.decode(item, q, u);
     if (u >= g.nverts(q)) {  // a caller-pushed item outside the graph: report and skip it
@@ -895,6 +976,18 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
         val = !V::kBatched ? rc.bfs_val
                            : (rc.ds != nullptr ? static_cast<uint32_t>(__ldcg(rc.ds + item) >> 32) : __ldcg(g.state + item)) + 1u;
       else val = __ldcg(g.state + item);
+    }
+  }
+  if constexpr (V::kBatched) {
+    if (g.lim != nullptr) {
+      // near-far: an SSSP item at or above its query's limit is not expanded
+      // now; it waits on the far list (once per round) until the limit passes it
+      const bool defer = valid && g.op(q) == OP_SSSP && val >= g.lim[q];
+      if (defer) {
+        valid = false;
+        beg = end = 0;
+      }
+      push_far_item<CTA>(g, sm, rc, defer, item, q);
     }
   }
   const uint32_t deg = end - beg;
@@ -1062,6 +1155,9 @@ __device__ __forceinline__ void round_body(const V& g, Smem<CTA>& sm, const Roun
     if (threadIdx.x == 0) sm.grab_base = static_end + atomicAdd(rc.grab, span);
     __syncthreads();
     gb = sm.grab_base;
+  }
+  if constexpr (V::kBatched) {
+    if (g.lim != nullptr && rc.far_in_n != 0) far_sweep<CTA>(g, sm, rc);
   }
   // CTA-local sub-rounds: expand the stage's newest items [lo, hi) here, with
   // CTA barriers only; their pushes land after them in the stage (or go global
@@ -1443,7 +1539,8 @@ __device__ __forceinline__ void fill_packed(unsigned long long* ds, uint32_t n, 
 template <int CTA>
 __device__ __forceinline__ void persistent_exit(Smem<CTA>& sm, DevStatus* st, bool ok, uint32_t rounds,
                                                 uint32_t last_out, uint32_t ep0, unsigned long long esum,
-                                                uint32_t* cont, uint32_t cont_buf) {
+                                                uint32_t* cont, uint32_t cont_buf, uint32_t far_buf = 0,
+                                                uint32_t far_n = 0) {
   __syncthreads();
   if (threadIdx.x == 0) {
     atomicAdd(&st->edges, esum);
@@ -1461,6 +1558,12 @@ __device__ __forceinline__ void persistent_exit(Smem<CTA>& sm, DevStatus* st, bo
     if (cont) {
       cont[0] = cont_buf;
       cont[1] = last_out;
+      cont[2] = far_buf;  // batched near-far: the far list left for the next launch
+      cont[3] = far_n;
+      for (int i = 0; i < 3; ++i) {
+        st->bfar_tail[i] = 0;
+        for (int w = 0; w < 32; ++w) st->qnear[i][w] = 0;
+      }
     }
     st->rounds = rounds;
     st->last_out = last_out;
@@ -1833,17 +1936,29 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
   const uint32_t ep0 = __ldcg(&st->epoch);
   const uint32_t cur0 = __ldcg(p.cont) & 1u;
   const uint32_t init_n = nq == 0 ? 0u : min(__ldcg(p.cont + 1), p.cap);
-  BatchView g{p.desc, bs.sbases, nq, p.state, p.stamp, bs.qbits};
-  if (threadIdx.x < kMaxBatchQueries / 32) bs.qbits[threadIdx.x] = 0;
+  // near-far (SSSP queries): limits in shared memory, advanced by delta after
+  // every round in which the query pushed nothing to the out-worklist
+  const bool nf = p.delta != 0 && p.ds != nullptr;
+  const uint32_t fcur0 = nf ? (__ldcg(p.cont + 2) & 1u) : 0u;
+  uint32_t far_n = nf ? min(__ldcg(p.cont + 3), p.far_cap) : 0u;
+  if (nf)
+    for (uint32_t i = threadIdx.x; i < nq; i += CTA) bs.lim[i] = __ldcg(p.blim + __ldg(&p.desc[i].slot));
+  BatchView g{p.desc, bs.sbases, nq, p.state, p.stamp, bs.qbits, bs.qfar, nf ? bs.lim : nullptr, p.far_stamp};
+  if (threadIdx.x < kMaxBatchQueries / 32) {
+    bs.qbits[threadIdx.x] = 0;
+    bs.qfar[threadIdx.x] = 0;
+  }
   __syncthreads();
-  // fold this CTA's query bits into the round's global bitmap (before a barrier)
+  // fold this CTA's query bits into the round's global bitmaps (before a barrier)
   auto fold_marks = [&](uint32_t r) {
     __syncthreads();
     for (uint32_t w = threadIdx.x; w < kMaxBatchQueries / 32; w += CTA) {
-      const uint32_t bits = bs.qbits[w];
-      if (bits) {
-        atomicOr(&st->qmask[r & 1][w], bits);
+      const uint32_t bits = bs.qbits[w], fbits = bs.qfar[w];
+      if (bits | fbits) {
+        atomicOr(&st->qmask[r & 1][w], bits | fbits);
+        if (nf && bits) atomicOr(&st->qnear[r % 3][w], bits);
         bs.qbits[w] = 0;
+        bs.qfar[w] = 0;
       }
     }
   };
@@ -1889,6 +2004,28 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
     rc.dsr = rc.ep;
     rc.local_rounds = 0;
     rc.local_items = nullptr;
+    rc.far_in = nullptr;
+    rc.far_in_n = 0;
+    if (nf) {
+      rc.far_in = p.far_items[(fcur0 + r) & 1u];
+      rc.far_in_n = far_n;
+      rc.far_out = Out{p.far_items[(fcur0 + r + 1) & 1u], &st->bfar_tail[(r + 1) % 3], p.far_cap, &st->err};
+      rc.far_stamp = p.far_stamp;
+      if (r != 0) {
+        // the previous round's out-worklist bits are complete after its barrier
+        for (uint32_t i = threadIdx.x; i < nq; i += CTA) {
+          const uint32_t slot = __ldg(&p.desc[i].slot);
+          if (!((__ldcg(&st->qnear[(r - 1) % 3][slot >> 5]) >> (slot & 31u)) & 1u))
+            bs.lim[i] = bs.lim[i] >= kInf - p.delta ? kInf : bs.lim[i] + p.delta;
+        }
+      }
+      // round r - 2's bitmap and round r - 1's far-in size were read before the last barrier
+      if (blockIdx.x == 0) {
+        for (uint32_t w = threadIdx.x; w < 32; w += CTA) st->qnear[(r + 1) % 3][w] = 0;
+        if (threadIdx.x == 0) st->bfar_tail[(r + 2) % 3] = 0;
+      }
+      __syncthreads();
+    }
     if (threadIdx.x == 0) {
       if (blockIdx.x == 0) {
         st->tail[(r + 2) % 3] = 0;
@@ -1910,16 +2047,20 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
     publish_marks(r, rc.ep);
     last_out = sm.pub_out;
     rounds = r + 1;
+    if (nf) far_n = min(__ldcg(&st->bfar_tail[(r + 1) % 3]), p.far_cap);
     trace_round(p.trace, p.trace_cap, rounds, in_n, last_out);
-    if (last_out == 0 || sm.pub_err != DERR_NONE) break;
+    if ((last_out == 0 && far_n == 0) || sm.pub_err != DERR_NONE) break;
     if (rounds >= p.max_rounds) {
       if (p.rounds_cap_is_error && blockIdx.x == 0 && threadIdx.x == 0) set_err(&st->err, DERR_MAX_ROUNDS);
       break;
     }
     in_n = min(last_out, p.cap);
   }
+  if (nf && blockIdx.x == 0)  // every CTA holds the same limits
+    for (uint32_t i = threadIdx.x; i < nq; i += CTA) p.blim[__ldg(&p.desc[i].slot)] = bs.lim[i];
   const unsigned long long esum = cta_sum_u64<CTA>(sm, edges);
-  persistent_exit<CTA>(sm, st, ok, rounds, last_out, ep0, esum, p.cont, (cur0 + rounds) & 1u);
+  persistent_exit<CTA>(sm, st, ok, rounds, last_out, ep0, esum, p.cont, (cur0 + rounds) & 1u,
+                       (fcur0 + rounds) & 1u, far_n);
 }
 
 // Admission of new queries into a batch: per new query j, arena range
@@ -1946,10 +2087,12 @@ struct AdmitParams {
   unsigned long long* ds; // packed arena (when set, the initial values go here)
   uint32_t* qlast;
   uint32_t* qfirst;       // optional, per query id: the round id it was admitted at
+  uint32_t* blim;         // optional (near-far): per slot limit, set to delta
   uint32_t* items[2];
   uint32_t cap;
   uint32_t* cont;
   DevStatus* st;
+  uint32_t delta;
 };
 
 __device__ __forceinline__ uint32_t find_new(const QNew* qn, uint32_t nnew, uint32_t i) {
@@ -2009,6 +2152,7 @@ __device__ __forceinline__ void admit_sources(const AdmitParams& a) {
   for (uint32_t j = tid; j < a.nnew; j += nthreads) {
     a.qlast[a.qn[j].slot] = ep - 1u;
     if (a.qfirst != nullptr) a.qfirst[a.qn[j].slot] = ep;
+    if (a.blim != nullptr) a.blim[a.qn[j].slot] = a.delta;
   }
   // one warp per new query walks its sources
   const uint32_t warp = tid >> 5, nwarps = nthreads >> 5, lane = threadIdx.x & 31;

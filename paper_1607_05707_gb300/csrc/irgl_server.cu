@@ -4,7 +4,8 @@
 // A host worker thread repeats:
 //   1. admission: take queued queries in arrival order while a slot is free and
 //      the query's state (20 bytes per vertex: the packed (value, round id)
-//      word, the u32 result and two worklist entries) fits in the device arena
+//      word, the u32 result and two worklist entries; 32 with near-far, which
+//      adds two far-list entries and a far stamp) fits in the device arena
 //      (first-fit over free ranges); the arena is sized from free HBM when the
 //      server starts;
 //   2. upload the sorted descriptor table of the active queries and the new
@@ -144,6 +145,9 @@ struct irgl_server {
   uint32_t* items[2] = {nullptr, nullptr};
   uint32_t* qlast = nullptr;
   uint32_t* cont = nullptr;
+  uint32_t* far_items[2] = {nullptr, nullptr};  // near-far (tuning delta != 0): far lists
+  uint32_t* far_stamp = nullptr;                //   arena: round id of the far list a vertex was last put on
+  uint32_t* blim = nullptr;                     //   per slot: the SSSP query's limit
   QDesc* desc = nullptr;
   uint32_t* sbases = nullptr;
   QNew* qnew = nullptr;
@@ -202,6 +206,10 @@ void server_free(irgl_server* s) {
   cudaFree(s->items[1]);
   cudaFree(s->qlast);
   cudaFree(s->cont);
+  cudaFree(s->far_items[0]);
+  cudaFree(s->far_items[1]);
+  cudaFree(s->far_stamp);
+  cudaFree(s->blim);
   cudaFree(s->desc);
   cudaFree(s->sbases);
   cudaFree(s->qnew);
@@ -343,6 +351,8 @@ bool server_step(irgl_server* s) {
     ap.cap = static_cast<uint32_t>(s->arena_n);
     ap.cont = s->cont;
     ap.st = s->st;
+    ap.blim = s->blim;
+    ap.delta = s->blim ? s->t.delta : 0u;
     e = cudaMemcpyAsync(s->qnew, s->h_qnew, sizeof(QNew) * fresh.size(), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(s->srcs, s->h_srcs, sizeof(uint32_t) * nsrc, cudaMemcpyHostToDevice, s->stream);
@@ -380,6 +390,12 @@ bool server_step(irgl_server* s) {
   bp.rounds_cap_is_error = 0;
   bp.timeout_ns = 2000000000ull;
   bp.big = (s->t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{s->big_e, s->big_off, s->big_cap};
+  bp.delta = s->blim ? s->t.delta : 0u;
+  bp.blim = s->blim;
+  bp.far_items[0] = s->far_items[0];
+  bp.far_items[1] = s->far_items[1];
+  bp.far_cap = s->blim ? static_cast<uint32_t>(s->arena_n) : 0u;
+  bp.far_stamp = s->far_stamp;
   if (e == cudaSuccess && nq) e = cudaEventRecord(s->ev[0], s->stream);
   if (e == cudaSuccess && nq) e = launch_batch_iterate(s->t.cta_size, s->grid, bp, s->stream);
   if (e == cudaSuccess && nq) e = cudaEventRecord(s->ev[1], s->stream);
@@ -512,7 +528,9 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
     bytes = static_cast<uint64_t>(fr * 0.4);
   }
   const bool packed = !(t.flags & IRGL_TUNE_NO_PACKED);
-  s->arena_n = std::min<uint64_t>(bytes / (packed ? 20 : 16), 0xFFFFFFF0ull);
+  // near-far for SSSP queries (packed words only): two far lists and a far stamp per vertex
+  const bool nf = packed && t.delta != 0;
+  s->arena_n = std::min<uint64_t>(bytes / (nf ? 32 : (packed ? 20 : 16)), 0xFFFFFFF0ull);
   const uint32_t S = cfg->max_slots;
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&s->ev[0]);
@@ -528,6 +546,10 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   if (e == cudaSuccess) e = cudaMalloc(&s->items[1], sizeof(uint32_t) * s->arena_n);
   if (e == cudaSuccess) e = cudaMalloc(&s->qlast, sizeof(uint32_t) * S);
   if (e == cudaSuccess) e = cudaMalloc(&s->cont, 128);
+  if (nf && e == cudaSuccess) e = cudaMalloc(&s->far_items[0], sizeof(uint32_t) * s->arena_n);
+  if (nf && e == cudaSuccess) e = cudaMalloc(&s->far_items[1], sizeof(uint32_t) * s->arena_n);
+  if (nf && e == cudaSuccess) e = cudaMalloc(&s->far_stamp, sizeof(uint32_t) * s->arena_n);
+  if (nf && e == cudaSuccess) e = cudaMalloc(&s->blim, sizeof(uint32_t) * S);
   if (e == cudaSuccess) e = cudaMalloc(&s->desc, sizeof(QDesc) * S);
   if (e == cudaSuccess) e = cudaMalloc(&s->sbases, sizeof(uint32_t) * S);
   if (e == cudaSuccess) e = cudaMalloc(&s->qnew, sizeof(QNew) * S);
@@ -554,6 +576,7 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   *s->st_host = z;
   e = cudaMemcpyAsync(s->st, s->st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess && s->stamp) e = cudaMemsetAsync(s->stamp, 0, sizeof(uint32_t) * s->arena_n, s->stream);
+  if (e == cudaSuccess && s->far_stamp) e = cudaMemsetAsync(s->far_stamp, 0, sizeof(uint32_t) * s->arena_n, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->cont, 0, 128, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->qlast, 0, sizeof(uint32_t) * S, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);

@@ -29,7 +29,7 @@ std::vector<Axis> axes(bool with_delta, bool with_local) {
       {&irgl_tuning::chunk, {1, 2, 4}},
       {&irgl_tuning::blocks_per_sm, {0, 1, 2, 4}},
   };
-  if (with_delta) a.push_back({&irgl_tuning::delta, {0, 16, 32, 64, 128, 256, 512}});
+  if (with_delta) a.push_back({&irgl_tuning::delta, {0, 16, 32, 64, 128, 256, 512, 1024}});
   // CTA-local sub-rounds; the only flag the search sets (the defaults have none)
   if (with_local) a.push_back({&irgl_tuning::flags, {0, IRGL_TUNE_LOCAL(4), IRGL_TUNE_LOCAL(15)}});
   return a;

@@ -112,6 +112,55 @@ def test_batch_waves_match_oracle(ctx, use_graph, wave_bytes):
         dg.close()
 
 
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("delta,wave_bytes", [(1, 0), (8, 0), (100, 0), (1000, 0), (64, 8 * 20000)])
+def test_batch_near_far_matches_oracle(ctx, use_graph, delta, wave_bytes):
+    """Per-query near-far for the SSSP queries of a mixed batch: same results, and
+    BFS queries keep their round counts."""
+    from paper_1607_05707_gb300.api import Batch
+
+    inst = _instances()
+    graphs = [ctx.load(g) for _, g, _ in inst]
+    b = Batch(ctx, 64)
+    for (k, g, s), dg in zip(inst, graphs):
+        b.add(k, dg, s)
+    b.prepare(dict(delta=delta), use_cuda_graph=use_graph, wave_bytes=wave_bytes)
+    for rep in range(2):
+        b.run()
+        for q, (k, g, s) in enumerate(inst):
+            got, rounds = b.result(q)
+            want = oracle.run(k, g, s)
+            np.testing.assert_array_equal(got, want, err_msg=f"query {q} ({k}) delta {delta} rep {rep}")
+            if k == "bfs":
+                assert rounds == int(want[want != INF].max()) + 1
+    b.close()
+    for dg in graphs:
+        dg.close()
+
+
+def test_batch_near_far_scans_fewer_edges(ctx):
+    """SSSP on a weighted mesh: label-correcting rounds re-relax most edges many
+    times; with per-query near-far the same 8 queries scan far fewer."""
+    from paper_1607_05707_gb300.api import Batch
+
+    g = inputs.mesh(160, 150, seed=11, del_frac=0.01, extra_frac=0.001, weights=True)
+    dg = ctx.load(g)
+    srcs = inputs.sources(g, 8, seed=12)
+    scanned = {}
+    for delta in (0, 128):
+        b = Batch(ctx, 8)
+        for s in srcs:
+            b.add("sssp", dg, [int(s)])
+        b.prepare(dict(delta=delta))
+        st = b.run()
+        scanned[delta] = st["edges_scanned"]
+        for q, s in enumerate(srcs):
+            np.testing.assert_array_equal(b.result(q)[0], oracle.run("sssp", g, np.array([s], np.uint32)))
+        b.close()
+    assert scanned[128] * 4 < scanned[0], scanned
+    dg.close()
+
+
 def test_batch_results_one_copy(ctx):
     from paper_1607_05707_gb300.api import Batch
 

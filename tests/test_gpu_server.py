@@ -76,6 +76,25 @@ def test_server_mix_matches_oracle(env):
     srv.close()
 
 
+@pytest.mark.parametrize("delta", [16, 128])
+def test_server_near_far_matches_oracle(env, delta):
+    """Per-query near-far for the SSSP queries (far lists carried across epochs):
+    results still bit-exact, BFS round counts unchanged."""
+    from paper_1607_05707_gb300.api import Server
+
+    ctx, graphs, dgs = env
+    qs = _queries(graphs, 48, seed=21)
+    srv = Server(ctx, arena_bytes=96 << 20, max_slots=16, epoch_rounds=8, tuning=dict(delta=delta))
+    bufs = [np.empty(graphs[gi].n, dtype=np.uint32) for _, gi, _ in qs]
+    tickets = [srv.submit(k, dgs[gi], s, b) for (k, gi, s), b in zip(qs, bufs)]
+    srv.drain(120)
+    for q, b, t in zip(qs, bufs, tickets):
+        _check(graphs, q, b, srv.poll(t))
+    st = srv.stats()
+    assert st["completed"] == len(qs) and st["rejected"] == 0
+    srv.close()
+
+
 def test_server_admission_by_memory(env):
     from paper_1607_05707_gb300 import irgl as C
     from paper_1607_05707_gb300.api import Server
