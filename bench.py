@@ -716,10 +716,11 @@ def run_serve(args, world, rank, local):
     sides = rng.integers(256, 2049, size=32)
     graphs += [inputs.mesh(int(sd), int(sd), seed=1005000 + i, weights=True) for i, sd in enumerate(sides)]
     # per-query near-far for the SSSP queries (delta 512: measured 3x the plain rounds' GTEPS
-    # on this mix, where grid SSSP re-relaxes each edge about 40 times)
-    tuning = json.loads(args.tuning) if args.tuning else {"delta": 512}
+    # on this mix, where grid SSSP re-relaxes each edge about 40 times); the R-MAT graph's BFS
+    # queries run alone and direction-optimising (in-edges loaded: 2.8 -> 1.5 ms at scale 24)
+    tuning = json.loads(args.tuning) if args.tuning else {"delta": 512, "flags": 2}
     ctx = Context(local, torch.cuda.Stream(device=dev))
-    dgs = [ctx.load(g, validate=False) for g in graphs]
+    dgs = [ctx.load(g, validate=False, in_edges=(i == 0)) for i, g in enumerate(graphs)]
     arrivals = inputs.poisson_arrivals(args.rate, args.duration, seed=2005 + rank)
     nq = len(arrivals)
     gi = rng.integers(0, len(graphs), size=nq)

@@ -132,6 +132,60 @@ __global__ void k_reached_edges(const uint32_t* __restrict__ state, const uint32
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
+// One finished query of an epoch: its arena range, the exclusive prefix of n
+// over the epoch's finished queries, its slot and its graph's row offsets.
+struct FinDesc {
+  const uint32_t* row_ptr;
+  uint32_t base, n, pre, slot;
+};
+
+// Every query that finished in an epoch at once: results from the packed words
+// (when ds is set) into the u32 arena and, with count_edges, the out-edges of
+// reached vertices per slot (one atomic per run of same-query lanes in a warp).
+__global__ void k_finish(const FinDesc* __restrict__ fd, uint32_t nf, uint32_t total,
+                         const unsigned long long* __restrict__ ds, uint32_t* state, unsigned long long* edge_cnt,
+                         int count_edges) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t nthreads = gridDim.x * blockDim.x;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (uint64_t w0 = tid - lane; w0 < total; w0 += nthreads) {  // warp-uniform trip count
+    const uint32_t i = static_cast<uint32_t>(w0) + lane;
+    uint32_t j = 0, e = 0;
+    if (i < total) {
+      uint32_t lo = 0, hi = nf - 1;
+      while (lo < hi) {
+        const uint32_t md = (lo + hi + 1) >> 1;
+        if (__ldg(&fd[md].pre) <= i) lo = md;
+        else hi = md - 1;
+      }
+      j = lo;
+      const uint32_t v = i - __ldg(&fd[j].pre);
+      const uint32_t item = __ldg(&fd[j].base) + v;
+      uint32_t val;
+      if (ds != nullptr) {
+        val = static_cast<uint32_t>(__ldcg(ds + item) >> 32);
+        __stcg(state + item, val);
+      } else {
+        val = __ldcg(state + item);
+      }
+      if (count_edges && val != kInf) {
+        const uint32_t* rp = fd[j].row_ptr;
+        e = __ldg(rp + v + 1) - __ldg(rp + v);
+      }
+    }
+    if (count_edges) {
+      const unsigned act = __ballot_sync(kFull, i < total);
+      if (i < total) {
+        // lanes of one query: their degrees summed in two 16-bit halves (no overflow in 32 lanes)
+        const unsigned grp = __match_any_sync(act, j);
+        const unsigned long long sum = static_cast<unsigned long long>(__reduce_add_sync(grp, e & 0xFFFFu)) +
+                                       (static_cast<unsigned long long>(__reduce_add_sync(grp, e >> 16)) << 16);
+        if (static_cast<uint32_t>(__ffs(grp) - 1) == lane && sum) atomicAdd(edge_cnt + fd[j].slot, sum);
+      }
+    }
+  }
+}
+
 struct irgl_server {
   irgl_ctx* ctx = nullptr;
   irgl_server_config cfg{};
@@ -153,6 +207,7 @@ struct irgl_server {
   QNew* qnew = nullptr;
   uint32_t* srcs = nullptr;
   unsigned long long* edge_cnt = nullptr;
+  FinDesc* fin = nullptr;              // the epoch's finished queries (k_finish)
   uint4* big_e = nullptr;
   unsigned long long* big_off = nullptr;
   uint32_t big_cap = 0;
@@ -163,6 +218,7 @@ struct irgl_server {
   uint32_t* h_srcs = nullptr;
   uint32_t* h_qlast = nullptr;
   unsigned long long* h_edges = nullptr;
+  FinDesc* h_fin = nullptr;
   uint32_t* h_scratch = nullptr;  // result sink for queries without a host buffer
   uint64_t scratch_n = 0;
   uint64_t arena_n = 0;
@@ -215,6 +271,7 @@ void server_free(irgl_server* s) {
   cudaFree(s->qnew);
   cudaFree(s->srcs);
   cudaFree(s->edge_cnt);
+  cudaFree(s->fin);
   cudaFree(s->big_e);
   cudaFree(s->big_off);
   if (s->st_host) cudaFreeHost(s->st_host);
@@ -224,6 +281,7 @@ void server_free(irgl_server* s) {
   if (s->h_srcs) cudaFreeHost(s->h_srcs);
   if (s->h_qlast) cudaFreeHost(s->h_qlast);
   if (s->h_edges) cudaFreeHost(s->h_edges);
+  if (s->h_fin) cudaFreeHost(s->h_fin);
   if (s->h_scratch) cudaFreeHost(s->h_scratch);
   if (s->ev[0]) cudaEventDestroy(s->ev[0]);
   if (s->ev[1]) cudaEventDestroy(s->ev[1]);
@@ -431,24 +489,32 @@ bool server_step(irgl_server* s) {
   for (auto& a : fin)
     if (!a.rq.host_out) need = std::max<uint64_t>(need, a.n);
   if (e == cudaSuccess) e = ensure_scratch(s, need);
-  for (auto& a : fin) {
-    uint32_t* dst = a.rq.host_out ? a.rq.host_out : s->h_scratch;
-    if (e == cudaSuccess && s->ds)
-      e = launch_extract_values(s->ds + a.base, s->state + a.base, a.n, static_cast<uint32_t>(s->ctx->sm_count) * 4,
-                                s->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(dst, s->state + a.base, sizeof(uint32_t) * (size_t)a.n, cudaMemcpyDeviceToHost, s->stream);
-    if (s->cfg.count_edges && e == cudaSuccess) {
-      e = cudaMemsetAsync(s->edge_cnt + a.slot, 0, sizeof(unsigned long long), s->stream);
-      if (e == cudaSuccess) {
-        k_reached_edges<<<static_cast<uint32_t>(s->ctx->sm_count), 256, 0, s->stream>>>(
-            s->state + a.base, a.rq.g->row_ptr, a.n, s->edge_cnt + a.slot);
-        e = cudaGetLastError();
-      }
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->h_edges + a.slot, s->edge_cnt + a.slot, sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, s->stream);
+  // every finished query's result and reached edges in one kernel, then one copy per result
+  if (!fin.empty()) {
+    uint64_t total = 0;
+    for (size_t k = 0; k < fin.size(); ++k) {
+      const Active& a = fin[k];
+      s->h_fin[k] = FinDesc{a.rq.g->row_ptr, a.base, a.n, static_cast<uint32_t>(total), a.slot};
+      total += a.n;
     }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->fin, s->h_fin, sizeof(FinDesc) * fin.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess && s->cfg.count_edges)
+      e = cudaMemsetAsync(s->edge_cnt, 0, sizeof(unsigned long long) * max_slots, s->stream);
+    if (e == cudaSuccess && total) {
+      k_finish<<<static_cast<uint32_t>(s->ctx->sm_count) * 4, 256, 0, s->stream>>>(
+          s->fin, static_cast<uint32_t>(fin.size()), static_cast<uint32_t>(total), s->ds, s->state, s->edge_cnt,
+          s->cfg.count_edges ? 1 : 0);
+      e = cudaGetLastError();
+    }
+    for (auto& a : fin) {
+      uint32_t* dst = a.rq.host_out ? a.rq.host_out : s->h_scratch;
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dst, s->state + a.base, sizeof(uint32_t) * (size_t)a.n, cudaMemcpyDeviceToHost, s->stream);
+    }
+    if (e == cudaSuccess && s->cfg.count_edges)
+      e = cudaMemcpyAsync(s->h_edges, s->edge_cnt, sizeof(unsigned long long) * max_slots, cudaMemcpyDeviceToHost,
+                          s->stream);
   }
   if (!fin.empty() && e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   const double t_done = now_s();
@@ -555,6 +621,7 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   if (e == cudaSuccess) e = cudaMalloc(&s->qnew, sizeof(QNew) * S);
   if (e == cudaSuccess) e = cudaMalloc(&s->srcs, sizeof(uint32_t) * S);
   if (e == cudaSuccess) e = cudaMalloc(&s->edge_cnt, sizeof(unsigned long long) * S);
+  if (e == cudaSuccess) e = cudaMalloc(&s->fin, sizeof(FinDesc) * S);
   if (e == cudaSuccess) {
     s->big_cap = big_capacity(s->arena_n);
     e = alloc_big(s->big_cap, &s->big_e, &s->big_off);
@@ -565,6 +632,7 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_srcs, sizeof(uint32_t) * S);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_qlast, sizeof(uint32_t) * S);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_edges, sizeof(unsigned long long) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_fin, sizeof(FinDesc) * S);
   if (e != cudaSuccess) {
     server_free(s);
     delete s;
