@@ -15,9 +15,11 @@
 //   3. one epoch: the batched persistent kernel runs at most epoch_rounds
 //      rounds over the union of all active queries' worklist items;
 //   4. queries that pushed nothing in the epoch's last round are finished:
-//      their result is copied to the caller's host buffer (or a scratch
-//      buffer), their completion time is stamped, and their arena range and
-//      slot are released.
+//      one kernel extracts all their results and counts their reached edges,
+//      then their results are copied to the callers' host buffers (or a
+//      scratch buffer) on a second stream while the next epochs run; once a
+//      copy has landed, the query's completion time is stamped and its arena
+//      range and slot are released (at most 8 epochs' copies in flight).
 // The host/device boundary is crossed once per epoch and every device wait is
 // bounded, so no kernel spins indefinitely while the server idles.
 //
@@ -69,6 +71,17 @@ struct Active {
   uint32_t n = 0;
   uint32_t epochs = 0;
   uint32_t ep_admit = 0;  // device epoch when admitted (round id base)
+};
+
+// Queries that finished in one epoch whose results are still being copied to
+// host memory on the copy stream: their slots and arena ranges are released,
+// and their completion published, once `ev` has completed.
+struct Pending {
+  std::vector<Active> fin;
+  std::vector<uint32_t> rounds;
+  unsigned long long* h_edges = nullptr;  // per slot, from the ring of pinned buffers
+  cudaEvent_t ev = nullptr;
+  uint32_t ring = 0;                       // ring entry holding h_edges and ev
 };
 
 struct Done {
@@ -190,6 +203,13 @@ struct irgl_server {
   irgl_ctx* ctx = nullptr;
   irgl_server_config cfg{};
   cudaStream_t stream = nullptr;
+  // result copies of finished queries run here, overlapping the next epochs
+  cudaStream_t copy_stream = nullptr;
+  static constexpr uint32_t kRing = 8;      // epochs whose copies may be in flight
+  unsigned long long* h_edge_ring = nullptr;  // kRing x max_slots pinned edge counts
+  cudaEvent_t ring_ev[kRing] = {};
+  std::vector<uint32_t> ring_free;
+  std::deque<Pending> pending;               // worker thread only
   // device
   DevStatus* st = nullptr;
   DevStatus* st_host = nullptr;
@@ -285,6 +305,10 @@ void server_free(irgl_server* s) {
   if (s->h_scratch) cudaFreeHost(s->h_scratch);
   if (s->ev[0]) cudaEventDestroy(s->ev[0]);
   if (s->ev[1]) cudaEventDestroy(s->ev[1]);
+  for (uint32_t i = 0; i < irgl_server::kRing; ++i)
+    if (s->ring_ev[i]) cudaEventDestroy(s->ring_ev[i]);
+  if (s->h_edge_ring) cudaFreeHost(s->h_edge_ring);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   cudaFree(s->solo_state);
   if (s->solo_ctx) irgl_ctx_destroy(s->solo_ctx);
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -293,6 +317,7 @@ void server_free(irgl_server* s) {
 // Ensure the pinned result sink holds n entries (worker thread only).
 cudaError_t ensure_scratch(irgl_server* s, uint64_t n) {
   if (n <= s->scratch_n) return cudaSuccess;
+  cudaStreamSynchronize(s->copy_stream);  // copies into the old sink may still be in flight
   if (s->h_scratch) cudaFreeHost(s->h_scratch);
   s->h_scratch = nullptr;
   s->scratch_n = 0;
@@ -363,13 +388,51 @@ void solo_step(irgl_server* s, const Request& rq) {
   s->cv_done.notify_all();
 }
 
+// Publish the queries of finished epochs whose result copies have completed
+// (in epoch order; `wait`: block on the oldest), releasing their slots and
+// arena ranges. Worker thread only.
+void retire_pending(irgl_server* s, bool wait) {
+  while (!s->pending.empty()) {
+    Pending& pd = s->pending.front();
+    cudaError_t e = wait ? cudaEventSynchronize(pd.ev) : cudaEventQuery(pd.ev);
+    if (e == cudaErrorNotReady) return;
+    const double t_done = now_s();
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (size_t k = 0; k < pd.fin.size(); ++k) {
+        const Active& a = pd.fin[k];
+        Done d;
+        d.status = e == cudaSuccess ? IRGL_OK : IRGL_ERR_CUDA;
+        d.rounds = pd.rounds[k];
+        d.t_submit = a.rq.t_submit;
+        d.t_done = t_done;
+        d.edges = s->cfg.count_edges ? pd.h_edges[a.slot] : 0;
+        s->edges_total += d.edges;
+        s->done[a.rq.ticket] = d;
+        s->completed += 1;
+        s->arena.release(a.base, a.n ? a.n : 1);
+        s->free_slots.push_back(a.slot);
+      }
+    }
+    s->ring_free.push_back(pd.ring);
+    s->pending.pop_front();
+    s->cv_done.notify_all();
+    wait = false;  // block on one epoch at most
+  }
+}
+
 // One scheduling step of the worker. Returns false when there was nothing to do.
 bool server_step(irgl_server* s) {
   const uint32_t max_slots = s->cfg.max_slots;
   std::vector<Active> fresh;
+  retire_pending(s, false);
   {
     std::unique_lock<std::mutex> lk(s->mu);
-    if (s->queue.empty() && s->active.empty()) return false;  // no batched work (the loop waits)
+    if (s->queue.empty() && s->active.empty()) {  // no batched work: finish the copies in flight
+      lk.unlock();
+      retire_pending(s, true);
+      return false;
+    }
     while (!s->queue.empty() && !s->free_slots.empty()) {
       Request& rq = s->queue.front();
       uint64_t base = 0;
@@ -489,16 +552,24 @@ bool server_step(irgl_server* s) {
   for (auto& a : fin)
     if (!a.rq.host_out) need = std::max<uint64_t>(need, a.n);
   if (e == cudaSuccess) e = ensure_scratch(s, need);
-  // every finished query's result and reached edges in one kernel, then one copy per result
-  if (!fin.empty()) {
+  // every finished query's result and reached edges in one kernel; the result
+  // copies run on the copy stream while the next epochs compute, and the
+  // queries are published (slots and arena released) once they have landed
+  if (!fin.empty() && e == cudaSuccess) {
+    if (s->ring_free.empty()) retire_pending(s, true);  // at most kRing epochs in flight
+    Pending pd;
+    pd.ring = s->ring_free.back();
+    s->ring_free.pop_back();
+    pd.h_edges = s->h_edge_ring + static_cast<size_t>(pd.ring) * max_slots;
+    pd.ev = s->ring_ev[pd.ring];
     uint64_t total = 0;
     for (size_t k = 0; k < fin.size(); ++k) {
       const Active& a = fin[k];
       s->h_fin[k] = FinDesc{a.rq.g->row_ptr, a.base, a.n, static_cast<uint32_t>(total), a.slot};
       total += a.n;
+      pd.rounds.push_back(s->h_qlast[a.slot] - a.ep_admit + 2);
     }
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s->fin, s->h_fin, sizeof(FinDesc) * fin.size(), cudaMemcpyHostToDevice, s->stream);
+    e = cudaMemcpyAsync(s->fin, s->h_fin, sizeof(FinDesc) * fin.size(), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess && s->cfg.count_edges)
       e = cudaMemsetAsync(s->edge_cnt, 0, sizeof(unsigned long long) * max_slots, s->stream);
     if (e == cudaSuccess && total) {
@@ -507,38 +578,34 @@ bool server_step(irgl_server* s) {
           s->cfg.count_edges ? 1 : 0);
       e = cudaGetLastError();
     }
+    if (e == cudaSuccess && s->cfg.count_edges)
+      e = cudaMemcpyAsync(pd.h_edges, s->edge_cnt, sizeof(unsigned long long) * max_slots, cudaMemcpyDeviceToHost,
+                          s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy_stream, pd.ev, 0);
     for (auto& a : fin) {
       uint32_t* dst = a.rq.host_out ? a.rq.host_out : s->h_scratch;
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dst, s->state + a.base, sizeof(uint32_t) * (size_t)a.n, cudaMemcpyDeviceToHost, s->stream);
+        e = cudaMemcpyAsync(dst, s->state + a.base, sizeof(uint32_t) * (size_t)a.n, cudaMemcpyDeviceToHost,
+                            s->copy_stream);
     }
-    if (e == cudaSuccess && s->cfg.count_edges)
-      e = cudaMemcpyAsync(s->h_edges, s->edge_cnt, sizeof(unsigned long long) * max_slots, cudaMemcpyDeviceToHost,
-                          s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->copy_stream);
+    pd.fin = std::move(fin);
+    s->pending.push_back(std::move(pd));
   }
-  if (!fin.empty() && e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   const double t_done = now_s();
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->epochs += 1;
     s->rounds_total += rounds;
     s->busy_s += t_done - t0;
-    for (auto& a : fin) {
-      Done d;
-      d.status = e == cudaSuccess ? IRGL_OK : IRGL_ERR_CUDA;
-      d.rounds = s->h_qlast[a.slot] - a.ep_admit + 2;
-      d.t_submit = a.rq.t_submit;
-      d.t_done = t_done;
-      d.edges = s->cfg.count_edges ? s->h_edges[a.slot] : 0;
-      s->edges_total += d.edges;
-      s->done[a.rq.ticket] = d;
-      s->completed += 1;
-      s->arena.release(a.base, a.n ? a.n : 1);
-      s->free_slots.push_back(a.slot);
+    if (e != cudaSuccess) {
+      s->fatal = IRGL_ERR_CUDA;
+      s->stop = true;
+      s->cv_done.notify_all();
     }
     s->active.swap(keep);
   }
-  if (!fin.empty()) s->cv_done.notify_all();
   return true;
 }
 
@@ -550,7 +617,7 @@ void server_loop(irgl_server* s) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->stop) break;
-      if (s->queue.empty() && s->active.empty() && s->solo_q.empty())
+      if (s->queue.empty() && s->active.empty() && s->solo_q.empty() && s->pending.empty())
         s->cv.wait_for(lk, std::chrono::milliseconds(2));
       if (s->stop) break;
     }
@@ -599,6 +666,13 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   s->arena_n = std::min<uint64_t>(bytes / (nf ? 32 : (packed ? 20 : 16)), 0xFFFFFFF0ull);
   const uint32_t S = cfg->max_slots;
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess)
+    e = cudaMallocHost(&s->h_edge_ring, sizeof(unsigned long long) * irgl_server::kRing * cfg->max_slots);
+  for (uint32_t i = 0; i < irgl_server::kRing && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&s->ring_ev[i], cudaEventDisableTiming);
+    s->ring_free.push_back(irgl_server::kRing - 1 - i);
+  }
   if (e == cudaSuccess) e = cudaEventCreate(&s->ev[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&s->ev[1]);
   if (e == cudaSuccess) e = cudaMalloc(&s->st, sizeof(DevStatus));
@@ -770,6 +844,7 @@ irgl_status irgl_server_destroy(irgl_server* s) {
   if (s->worker.joinable()) s->worker.join();
   DeviceGuard guard(s->ctx->device);
   cudaStreamSynchronize(s->stream);
+  if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
   server_free(s);
   delete s;
   return IRGL_OK;
