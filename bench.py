@@ -50,7 +50,8 @@ def parse_args():
     ap.add_argument("--workload", choices=["rmat20", "grid64", "mesh", "batch256", "serve", "msf"], default="rmat20")
     ap.add_argument("--msf-graph", choices=["mesh", "rmat"], default="mesh",
                     help="msf: the weighted 4096^2 mesh or a symmetrised R-MAT scale-20 graph")
-    ap.add_argument("--msf-lock", choices=["blocking", "ticket", "retry"], default="blocking")
+    ap.add_argument("--msf-lock", choices=["blocking", "ticket", "retry"], default="retry",
+                    help="msf: lock form (retry measured fastest on the 4096^2 mesh: 25.8 ms against 39.8 blocking)")
     ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
     ap.add_argument("--wave-mb", type=int, default=None,
                     help="batch256: packed-state MB per wave (-1: every instance in one wave; default: one wave, "
