@@ -44,7 +44,8 @@ INF = 0xFFFFFFFF
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 16; grid64: 1000, the median of 1000 repetitions)")
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=["rmat20", "grid64", "mesh", "batch256", "serve", "msf"], default="rmat20")
@@ -85,7 +86,10 @@ def parse_args():
     ap.add_argument("--local", type=int, default=-1,
                     help="CTA-local sub-rounds for persistent BFS/SSSP (0..15; default: 15 on the high-diameter "
                          "grid64 and mesh workloads, 0 on R-MAT, as the autotuner picks them)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 1000 if args.workload == "grid64" else 16
+    return args
 
 
 # ----------------------------------------------------------------------------- distributed plumbing
@@ -278,6 +282,25 @@ def peaks():
 
 # ----------------------------------------------------------------------------- CPU oracle timing
 
+def host_cpu() -> str:
+    """The host CPU's model, for the CPU baseline lines (first 'model name' / 'Model name' found)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_oracle_sample(g, srcs, kernels, budget_s: float):
     import oracle
 
@@ -293,7 +316,7 @@ def cpu_oracle_sample(g, srcs, kernels, budget_s: float):
         if t_total >= budget_s:
             break
     nq = len(done)
-    return {"value": edges / t_total / 1e9 if t_total > 0 else 0.0, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+    return {"value": edges / t_total / 1e9 if t_total > 0 else 0.0, "unit": "GTEPS", "cores": 1, "kind": "oracle", "cpu": host_cpu(),
             "sample": f"{nq} queries ({'+'.join(kernels)} from {nq // len(kernels)} of the workload's sources), "
                       f"{t_total:.1f} s serial on {platform.machine()} host ({os.cpu_count()} cores present, 1 used)"}
 
@@ -329,7 +352,7 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_sum / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": dict(workload=name, **meta, parallelism="rank 0 only (serial CPU oracle)"),
-        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "cpu": host_cpu(),
                          "sample": f"each step = {'+'.join(kernels)} from one source, serial"},
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -352,7 +375,7 @@ def run_reference_msf(args):
         "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * t_sum / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": name, "V": g.n, "m": g.m, "parallelism": "rank 0 only (serial CPU oracle)"},
-        "cpu_baseline": {"value": value, "unit": "G input edges/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "G input edges/s", "cores": 1, "kind": "oracle", "cpu": host_cpu(),
                          "sample": "each step = one Kruskal run on the whole graph, serial"},
         "e2e": {"value": value, "unit": "G input edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -662,7 +685,7 @@ def run_batch(args, world, rank, local):
             nq += 1
             if tt > args.cpu_budget:
                 break
-        cpu = {"value": ee / tt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+        cpu = {"value": ee / tt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle", "cpu": host_cpu(),
                "sample": f"first {nq} instances (serial Dijkstra), {tt:.1f} s on {platform.machine()} host"}
     hbm, peak_src = peaks()
     nbytes = sum(alg_bytes("sssp", g.n, int((b.result(q)[0] != INF).sum()), m) for q, ((g, _), m) in enumerate(zip(inst, mR)))
@@ -864,7 +887,7 @@ def run_msf(args, world, rank, local):
         t0 = time.perf_counter()
         oracle.msf(g.n, g.row_ptr, g.col, g.w)
         tc = time.perf_counter() - t0
-        cpu = {"value": g.m / tc / 1e9, "unit": "G input edges/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": g.m / tc / 1e9, "unit": "G input edges/s", "cores": 1, "kind": "oracle", "cpu": host_cpu(),
                "sample": f"one Kruskal run on the whole graph ({g.m} CSR entries), {tc:.1f} s serial"}
     hbm, peak_src = peaks()
     nbytes = 12 * g.m + 16 * g.n  # col + w + comp[v] per CSR entry, row_ptr pair + comp[u] + record per vertex
