@@ -54,6 +54,9 @@ def parse_args():
     ap.add_argument("--msf-lock", choices=["blocking", "ticket", "retry"], default="retry",
                     help="msf: lock form (retry measured fastest on the 4096^2 mesh: 25.8 ms against 39.8 blocking)")
     ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
+    ap.add_argument("--batch-set", choices=["rmat", "grids"], default="rmat",
+                    help="batch256: the R-MAT SSSP instances, or 32 serving-like queries on 16 weighted grids "
+                         "(side U[256,1024], 70%% BFS / 30%% SSSP)")
     ap.add_argument("--wave-mb", type=int, default=None,
                     help="batch256: packed-state MB per wave (-1: every instance in one wave; default: one wave, "
                          "or what the autotuner picks)")
@@ -590,19 +593,29 @@ def run_batch(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    inst_all = inputs_workload_batch(args.instances)
+    if args.batch_set == "grids":
+        from paper_1607_05707_gb300 import inputs
+
+        inst_all = inputs.workload_grid_batch()
+        tuning = json.loads(args.tuning) if args.tuning else None
+    else:
+        inst_all = [(g, s, "sssp") for g, s in inputs_workload_batch(args.instances)]
+        tuning = json.loads(args.tuning) if args.tuning else None
     inst = shard(inst_all, world, rank)
-    tuning = json.loads(args.tuning) if args.tuning else None
     stream = torch.cuda.Stream(device=dev)
     ctx = Context(local, stream)
-    dgs = [ctx.load(g, validate=False) for g, _ in inst]
+    loaded = {}  # queries on one graph share its device copy
+    for g, _, _ in inst:
+        if id(g) not in loaded:
+            loaded[id(g)] = ctx.load(g, validate=False)
+    dgs = [loaded[id(g)] for g, _, _ in inst]
     b = Batch(ctx, max(len(inst), 1))
-    for (g, s), dg in zip(inst, dgs):
-        b.add("sssp", dg, s)
+    for (g, s, k), dg in zip(inst, dgs):
+        b.add(k, dg, s)
     wave_bytes = 0 if args.wave_mb is None else ((1 << 64) - 1 if args.wave_mb < 0 else args.wave_mb << 20)
     info = b.prepare(tuning, use_cuda_graph=True, wave_bytes=wave_bytes)
     autotuned = None
-    if not args.no_autotune and tuning is None and args.wave_mb is None:
+    if not args.no_autotune and not args.tuning and args.wave_mb is None:
         # the batch is left prepared with the fastest tuning and wave budget (outside the timed region)
         t0 = time.perf_counter()
         tuning, tune_ms = b.autotune(reps=2)
@@ -610,7 +623,7 @@ def run_batch(args, world, rank, local):
         autotuned = {"search_s": round(time.perf_counter() - t0, 1), "median_ms": round(tune_ms, 3)}
     b.run()
     mR = []
-    for q, (g, s) in enumerate(inst):
+    for q, (g, s, _) in enumerate(inst):
         res, _ = b.result(q)
         mR.append(reached_stats(g, res)[1])
     edges = float(sum(mR))
@@ -631,14 +644,14 @@ def run_batch(args, world, rank, local):
     t_batch = max_over_ranks(sum(times) / len(times), world, dev)
     value = sum_over_ranks(edges, world, dev) / t_batch / 1e9
     # the same queries, one persistent launch each (host waits for each query's status)
-    outs = [ctx.state(g.n) for g, _ in inst]
+    outs = [ctx.state(g.n) for g, _, _ in inst]
     wls = []
-    for (g, s) in inst:
+    for (g, s, _) in inst:
         wl = ctx.worklist(8)
         wl.push(s)
         wls.append(wl)
     for q in range(min(8, len(inst))):
-        ctx.iterate_async("sssp", dgs[q], wls[q], outs[q], tuning=tuning)
+        ctx.iterate_async(inst[q][2], dgs[q], wls[q], outs[q], tuning=tuning)
         ctx.sync()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -647,7 +660,7 @@ def run_batch(args, world, rank, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx.iterate_async("sssp", dgs[q], wls[q], outs[q], tuning=tuning)
+        ctx.iterate_async(inst[q][2], dgs[q], wls[q], outs[q], tuning=tuning)
         e1.record(stream)
         ctx.sync()
         dev_sum += e0.elapsed_time(e1) * 1e-3
@@ -658,7 +671,7 @@ def run_batch(args, world, rank, local):
     seq_gteps = sum_over_ranks(edges, world, dev) / max_over_ranks(t_seq, world, dev) / 1e9
     seq_dev_gteps = sum_over_ranks(edges, world, dev) / max_over_ranks(dev_sum, world, dev) / 1e9
     # e2e: one batched run plus one copy of every instance's result into pinned host memory
-    total_n = sum(g.n for g, _ in inst)
+    total_n = sum(g.n for g, _, _ in inst)
     host = torch.empty(max(total_n, 1), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
     t_e2e_all = []
     for _ in range(3):
@@ -677,34 +690,36 @@ def run_batch(args, world, rank, local):
         import oracle
 
         tt, ee, nq = 0.0, 0, 0
-        for (g, s), m in zip(inst, mR):
+        for (g, s, k), m in zip(inst, mR):
             t1 = time.perf_counter()
-            oracle.sssp(g.n, g.row_ptr, g.col, g.w, s)
+            oracle.run(k, g, s)
             tt += time.perf_counter() - t1
             ee += m
             nq += 1
             if tt > args.cpu_budget:
                 break
         cpu = {"value": ee / tt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle", "cpu": host_cpu(),
-               "sample": f"first {nq} instances (serial Dijkstra), {tt:.1f} s on {platform.machine()} host"}
+               "sample": f"first {nq} instances (serial BFS / Dijkstra), {tt:.1f} s on {platform.machine()} host"}
     hbm, peak_src = peaks()
-    nbytes = sum(alg_bytes("sssp", g.n, int((b.result(q)[0] != INF).sum()), m) for q, ((g, _), m) in enumerate(zip(inst, mR)))
+    nbytes = sum(alg_bytes(k, g.n, int((b.result(q)[0] != INF).sum()), m) for q, ((g, _, k), m) in enumerate(zip(inst, mR)))
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * t_batch, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": dict(workload=f"batch{args.instances}: SSSP instances, R-MAT scale U{{10..18}}, edge factor 8, "
-                                    f"1-4 sources, w in [1,100]; one CUDA-graph replay of "
-                                    f"{info['waves']} wave(s), one persistent launch each",
+            "config": dict(workload=(f"batch{args.instances}: SSSP instances, R-MAT scale U{{10..18}}, edge factor 8, "
+                                     f"1-4 sources, w in [1,100]" if args.batch_set == "rmat" else
+                                     "grids32: 32 queries (70% BFS / 30% SSSP, uniform sources) on 16 weighted 4-neighbour "
+                                     "grids of side U[256,1024], w in [1,100]")
+                                    + f"; one CUDA-graph replay of {info['waves']} wave(s), one persistent launch each",
                            instances=len(inst_all), edges_out_of_reached=int(edges), batch=info,
                            parallelism=f"instances sharded x{world}", l2="flushed between steps (512 MB write)",
-                           tuning=tuning or ctx.default_tuning, autotuned=autotuned),
+                           tuning={**ctx.default_tuning, **(tuning or {})}, autotuned=autotuned),
             "per_launch": {"gteps_wall": round(seq_gteps, 4), "gteps_device": round(seq_dev_gteps, 4),
                            "form": "same instances, one persistent launch each, host waits per query"},
             "batched_vs_per_launch": round(value / seq_gteps, 3),
             "e2e": {"value": round(e2e, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": int(4 * sum(g.n for g, _ in inst))},
+                    "d2h_bytes_per_step": int(4 * sum(g.n for g, _, _ in inst))},
             "gpu_launches": (3 * info["waves"] + 1) * args.steps,
             "roofline": {"bound": "hbm", "achieved": round(nbytes / t_batch / 1e9, 2), "peak": hbm, "unit": "GB/s",
                          "frac": round(nbytes / t_batch / 1e9 / hbm, 4), "traffic": measured_traffic("k_batch_iterate"),

@@ -189,6 +189,22 @@ def workload_batch(count: int = 256, lo: int = 10, hi: int = 18, ef: int = 8):
     return out
 
 
+def workload_grid_batch(count: int = 32, graphs: int = 16, lo: int = 256, hi: int = 1024):
+    """Serving-like batch of high-diameter queries: `graphs` weighted 4-neighbour grids of side U[lo, hi]
+    and `count` single-source queries on them, 70% BFS / 30% SSSP, uniform sources.
+    Returns [(graph, sources, kind)]; queries on one mesh share its CSR object."""
+    rng = np.random.default_rng(2005)
+    sides = rng.integers(lo, hi + 1, size=graphs)
+    meshes = [mesh(int(sd), int(sd), seed=1005000 + i, weights=True) for i, sd in enumerate(sides)]
+    gi = rng.integers(0, graphs, size=count)
+    kinds = np.where(rng.random(count) < 0.7, "bfs", "sssp")
+    out = []
+    for i in range(count):
+        g = meshes[gi[i]]
+        out.append((g, np.array([int(rng.integers(0, g.n))], np.uint32), str(kinds[i])))
+    return out
+
+
 def poisson_arrivals(rate_hz: float, duration_s: float, seed: int = 2005) -> np.ndarray:
     """Arrival times (seconds) of a Poisson process of the given rate over [0, duration)."""
     rng = np.random.default_rng(seed)
