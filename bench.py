@@ -756,8 +756,9 @@ def run_serve(args, world, rank, local):
     graphs += [inputs.mesh(int(sd), int(sd), seed=1005000 + i, weights=True) for i, sd in enumerate(sides)]
     # per-query near-far for the SSSP queries (delta 512: measured 3x the plain rounds' GTEPS
     # on this mix, where grid SSSP re-relaxes each edge about 40 times); the R-MAT graph's BFS
-    # queries run alone and direction-optimising (in-edges loaded: 2.8 -> 1.5 ms at scale 24)
-    tuning = json.loads(args.tuning) if args.tuning else {"delta": 512, "flags": 2}
+    # queries run alone and direction-optimising (in-edges loaded: 2.8 -> 1.5 ms at scale 24);
+    # CTAs of 1024 (10 s of arrivals: 26.8 GTEPS, p50 340 ms, against 26.0 and 564 ms with 128)
+    tuning = json.loads(args.tuning) if args.tuning else {"delta": 512, "flags": 2, "cta_size": 1024}
     ctx = Context(local, torch.cuda.Stream(device=dev))
     dgs = [ctx.load(g, validate=False, in_edges=(i == 0)) for i, g in enumerate(graphs)]
     arrivals = inputs.poisson_arrivals(args.rate, args.duration, seed=2005 + rank)

@@ -82,6 +82,10 @@ struct Pending {
   unsigned long long* h_edges = nullptr;  // per slot, from the ring of pinned buffers
   cudaEvent_t ev = nullptr;
   uint32_t ring = 0;                       // ring entry holding h_edges and ev
+  // a query that ran alone: its request, rounds and edge count (h_edges[0])
+  bool solo = false;
+  Request rq;
+  uint32_t solo_rounds = 0;
 };
 
 struct Done {
@@ -266,8 +270,10 @@ struct irgl_server {
   uint32_t solo_min_n = 0xFFFFFFFFu;
   irgl_ctx* solo_ctx = nullptr;
   std::deque<Request> solo_q;
-  uint32_t* solo_state = nullptr;  // device result buffer (solo_cap entries)
-  uint64_t solo_cap = 0;
+  uint32_t* solo_state[2] = {nullptr, nullptr};  // device result buffers, alternated so a
+  uint64_t solo_cap[2] = {0, 0};                  // result copy overlaps the next solo query
+  cudaEvent_t solo_copied[2] = {nullptr, nullptr};  // the last copy out of each buffer
+  uint32_t solo_next = 0;
   uint64_t solo_done = 0;
 };
 
@@ -309,7 +315,10 @@ void server_free(irgl_server* s) {
     if (s->ring_ev[i]) cudaEventDestroy(s->ring_ev[i]);
   if (s->h_edge_ring) cudaFreeHost(s->h_edge_ring);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
-  cudaFree(s->solo_state);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(s->solo_state[i]);
+    if (s->solo_copied[i]) cudaEventDestroy(s->solo_copied[i]);
+  }
   if (s->solo_ctx) irgl_ctx_destroy(s->solo_ctx);
   if (s->stream) cudaStreamDestroy(s->stream);
 }
@@ -328,22 +337,36 @@ cudaError_t ensure_scratch(irgl_server* s, uint64_t n) {
 
 // One query alone: persistent single-query Iterate on the private context,
 // then the reached-edge count and the result copy, all on the server's stream.
+void retire_pending(irgl_server* s, bool wait);
+
+// One query on a large graph, alone: a persistent single-query Iterate on the
+// private context (the server's stream), its reached edges counted, then its
+// result copied to host memory on the copy stream while the worker moves on;
+// the query is published when the copy lands. Two result buffers alternate,
+// the stream waiting for a buffer's last copy before reusing it.
 void solo_step(irgl_server* s, const Request& rq) {
   const double t0 = now_s();
   const uint32_t n = rq.g->n;
+  const uint32_t k = s->solo_next;
+  s->solo_next ^= 1u;
   cudaError_t e = cudaSuccess;
-  if (n > s->solo_cap) {
-    cudaFree(s->solo_state);
-    s->solo_state = nullptr;
-    s->solo_cap = 0;
-    e = cudaMalloc(&s->solo_state, sizeof(uint32_t) * std::max<uint32_t>(n, 4));
-    if (e == cudaSuccess) s->solo_cap = n;
+  if (!s->solo_copied[k]) e = cudaEventCreateWithFlags(&s->solo_copied[k], cudaEventDisableTiming);
+  if (e == cudaSuccess && n > s->solo_cap[k]) {
+    cudaEventSynchronize(s->solo_copied[k]);  // nothing may still read the old buffer
+    cudaFree(s->solo_state[k]);
+    s->solo_state[k] = nullptr;
+    s->solo_cap[k] = 0;
+    e = cudaMalloc(&s->solo_state[k], sizeof(uint32_t) * std::max<uint32_t>(n, 4));
+    if (e == cudaSuccess) s->solo_cap[k] = n;
   }
   uint32_t* dst = rq.host_out;
   if (!dst && e == cudaSuccess) {
     e = ensure_scratch(s, n);
     dst = s->h_scratch;
   }
+  if (e == cudaSuccess && s->ring_free.empty()) retire_pending(s, true);
+  // the buffer's previous result copy finishes before this query writes it
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->solo_copied[k], 0);
   irgl_stats st;
   std::memset(&st, 0, sizeof(st));
   irgl_status r = e == cudaSuccess ? IRGL_OK : IRGL_ERR_OOM;
@@ -351,41 +374,57 @@ void solo_step(irgl_server* s, const Request& rq) {
   if (r == IRGL_OK) {
     cudaEventRecord(s->ev[0], s->stream);
     const uint32_t src = rq.src;
-    r = irgl_run(s->solo_ctx, static_cast<irgl_kernel>(rq.op), rq.g, &src, 1, s->solo_state, 0, IRGL_PERSISTENT,
+    r = irgl_run(s->solo_ctx, static_cast<irgl_kernel>(rq.op), rq.g, &src, 1, s->solo_state[k], 0, IRGL_PERSISTENT,
                  nullptr, 0, &st);
     cudaEventRecord(s->ev[1], s->stream);
   }
   if (r == IRGL_OK) {
+    Pending pd;
+    pd.solo = true;
+    pd.rq = rq;
+    pd.solo_rounds = st.rounds;
+    pd.ring = s->ring_free.back();
+    s->ring_free.pop_back();
+    pd.h_edges = s->h_edge_ring + static_cast<size_t>(pd.ring) * s->cfg.max_slots;
+    pd.ev = s->ring_ev[pd.ring];
     e = cudaMemsetAsync(s->edge_cnt, 0, sizeof(unsigned long long), s->stream);
     if (e == cudaSuccess && s->cfg.count_edges) {
-      k_reached_edges<<<static_cast<uint32_t>(s->ctx->sm_count), 256, 0, s->stream>>>(s->solo_state, rq.g->row_ptr, n,
-                                                                                     s->edge_cnt);
+      k_reached_edges<<<static_cast<uint32_t>(s->ctx->sm_count), 256, 0, s->stream>>>(s->solo_state[k],
+                                                                                     rq.g->row_ptr, n, s->edge_cnt);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s->h_edges, s->edge_cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream);
+      e = cudaMemcpyAsync(pd.h_edges, s->edge_cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy_stream, pd.ev, 0);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(dst, s->solo_state, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e == cudaSuccess) cudaEventElapsedTime(&kms, s->ev[0], s->ev[1]);
-    if (e != cudaSuccess) r = IRGL_ERR_CUDA;
+      e = cudaMemcpyAsync(dst, s->solo_state[k], sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost,
+                          s->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->solo_copied[k], s->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->copy_stream);
+    if (e == cudaSuccess) cudaEventElapsedTime(&kms, s->ev[0], s->ev[1]);  // irgl_run waited for the kernel
+    if (e == cudaSuccess) {
+      s->pending.push_back(std::move(pd));
+    } else {
+      s->ring_free.push_back(pd.ring);
+      r = IRGL_ERR_CUDA;
+    }
   }
   const double t_done = now_s();
   std::lock_guard<std::mutex> lk(s->mu);
-  Done d;
-  d.status = r;
-  d.rounds = st.rounds;
-  d.t_submit = rq.t_submit;
-  d.t_done = t_done;
-  d.edges = (r == IRGL_OK && s->cfg.count_edges) ? s->h_edges[0] : 0;
-  s->edges_total += d.edges;
   s->rounds_total += st.rounds;
   s->busy_s += t_done - t0;
   s->kernel_s += kms * 1e-3;
-  s->done[rq.ticket] = d;
-  s->completed += 1;
-  s->solo_done += 1;
-  s->cv_done.notify_all();
+  if (r != IRGL_OK) {  // published now, with its error
+    Done d;
+    d.status = r;
+    d.t_submit = rq.t_submit;
+    d.t_done = t_done;
+    s->done[rq.ticket] = d;
+    s->completed += 1;
+    s->solo_done += 1;
+    s->cv_done.notify_all();
+  }
 }
 
 // Publish the queries of finished epochs whose result copies have completed
@@ -397,7 +436,19 @@ void retire_pending(irgl_server* s, bool wait) {
     cudaError_t e = wait ? cudaEventSynchronize(pd.ev) : cudaEventQuery(pd.ev);
     if (e == cudaErrorNotReady) return;
     const double t_done = now_s();
-    {
+    if (pd.solo) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      Done d;
+      d.status = e == cudaSuccess ? IRGL_OK : IRGL_ERR_CUDA;
+      d.rounds = pd.solo_rounds;
+      d.t_submit = pd.rq.t_submit;
+      d.t_done = t_done;
+      d.edges = (e == cudaSuccess && s->cfg.count_edges) ? pd.h_edges[0] : 0;
+      s->edges_total += d.edges;
+      s->done[pd.rq.ticket] = d;
+      s->completed += 1;
+      s->solo_done += 1;
+    } else {
       std::lock_guard<std::mutex> lk(s->mu);
       for (size_t k = 0; k < pd.fin.size(); ++k) {
         const Active& a = pd.fin[k];
