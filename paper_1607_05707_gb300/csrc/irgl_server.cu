@@ -13,7 +13,10 @@
 //      append their sources to the pending worklist, which still holds the
 //      unfinished work of the queries already running;
 //   3. one epoch: the batched persistent kernel runs at most epoch_rounds
-//      rounds over the union of all active queries' worklist items;
+//      rounds over the union of all active queries' worklist items; the next
+//      step launches the following epoch before it reads this one back, so
+//      the host's bookkeeping overlaps the GPU's work (a query found finished
+//      one epoch late sat inert in that epoch: it had no items);
 //   4. queries that pushed nothing in the epoch's last round are finished:
 //      one kernel extracts all their results and counts their reached edges,
 //      then their results are copied to the callers' host buffers (or a
@@ -70,7 +73,12 @@ struct Active {
   uint32_t base = 0;
   uint32_t n = 0;
   uint32_t epochs = 0;
-  uint32_t ep_admit = 0;  // device epoch when admitted (round id base)
+};
+
+// An epoch launched and not yet read back: the queries it ran over.
+struct EpochRec {
+  bool live = false;
+  std::vector<Active> set;
 };
 
 // Queries that finished in one epoch whose results are still being copied to
@@ -216,7 +224,7 @@ struct irgl_server {
   std::deque<Pending> pending;               // worker thread only
   // device
   DevStatus* st = nullptr;
-  DevStatus* st_host = nullptr;
+  DevStatus* st_host = nullptr;        // pinned, two: one per launch parity
   uint32_t* state = nullptr;           // results (extracted from ds when a query finishes)
   uint32_t* stamp = nullptr;           // two-array form only (IRGL_TUNE_NO_PACKED)
   unsigned long long* ds = nullptr;    // packed (value, round id) arena
@@ -236,13 +244,22 @@ struct irgl_server {
   unsigned long long* big_off = nullptr;
   uint32_t big_cap = 0;
   // pinned staging
+  // pinned staging, two halves of max_slots entries each (by launch parity), so an epoch's
+  // uploads and read-backs never share a buffer with the next epoch's
   QDesc* h_desc = nullptr;
   uint32_t* h_sbases = nullptr;
   QNew* h_qnew = nullptr;
   uint32_t* h_srcs = nullptr;
   uint32_t* h_qlast = nullptr;
+  uint32_t* h_qfirst = nullptr;
   unsigned long long* h_edges = nullptr;
   FinDesc* h_fin = nullptr;
+  uint32_t* qfirst = nullptr;  // device, per slot: the round id the query was admitted at
+  // epochs in flight: epoch k+1 is launched before epoch k is read back
+  EpochRec rec[2];
+  uint32_t par = 0;            // parity of the next launch
+  cudaEvent_t ep_ev[4] = {};   // start / end of the epoch kernel, per parity
+  cudaEvent_t st_ev[2] = {};   // the epoch's status read-back has landed, per parity
   uint32_t* h_scratch = nullptr;  // result sink for queries without a host buffer
   uint64_t scratch_n = 0;
   uint64_t arena_n = 0;
@@ -311,6 +328,12 @@ void server_free(irgl_server* s) {
   if (s->h_scratch) cudaFreeHost(s->h_scratch);
   if (s->ev[0]) cudaEventDestroy(s->ev[0]);
   if (s->ev[1]) cudaEventDestroy(s->ev[1]);
+  for (int i = 0; i < 4; ++i)
+    if (s->ep_ev[i]) cudaEventDestroy(s->ep_ev[i]);
+  for (int i = 0; i < 2; ++i)
+    if (s->st_ev[i]) cudaEventDestroy(s->st_ev[i]);
+  cudaFree(s->qfirst);
+  if (s->h_qfirst) cudaFreeHost(s->h_qfirst);
   for (uint32_t i = 0; i < irgl_server::kRing; ++i)
     if (s->ring_ev[i]) cudaEventDestroy(s->ring_ev[i]);
   if (s->h_edge_ring) cudaFreeHost(s->h_edge_ring);
@@ -472,14 +495,21 @@ void retire_pending(irgl_server* s, bool wait) {
   }
 }
 
-// One scheduling step of the worker. Returns false when there was nothing to do.
+// One scheduling step of the worker: admit, launch the next epoch over every
+// active query, then read back the epoch launched by the previous step (its
+// status copies precede this launch on the stream, so the GPU stays busy while
+// the host decides which of its queries finished). A query found finished is
+// inert in the epoch already running (it has no items), and is dropped from the
+// following one. Returns false when there was nothing to do.
 bool server_step(irgl_server* s) {
-  const uint32_t max_slots = s->cfg.max_slots;
+  const uint32_t S = s->cfg.max_slots;
+  const uint32_t p = s->par;  // parity of this step's launch
+  const uint32_t q = p ^ 1u;  // the epoch launched by the previous step
   std::vector<Active> fresh;
   retire_pending(s, false);
   {
     std::unique_lock<std::mutex> lk(s->mu);
-    if (s->queue.empty() && s->active.empty()) {  // no batched work: finish the copies in flight
+    if (s->queue.empty() && s->active.empty() && !s->rec[q].live) {  // no batched work: finish the copies
       lk.unlock();
       retire_pending(s, true);
       return false;
@@ -494,7 +524,6 @@ bool server_step(irgl_server* s) {
       s->free_slots.pop_back();
       a.base = static_cast<uint32_t>(base);
       a.n = rq.g->n;
-      a.ep_admit = s->st_host->epoch;  // first round id of the next epoch
       fresh.push_back(a);
       s->queue.pop_front();
     }
@@ -503,11 +532,13 @@ bool server_step(irgl_server* s) {
   cudaError_t e = cudaSuccess;
   // admission of new queries: descriptors, sources, initial values, pending items
   if (!fresh.empty()) {
+    QNew* hq = s->h_qnew + static_cast<size_t>(p) * S;
+    uint32_t* hs = s->h_srcs + static_cast<size_t>(p) * S;
     uint32_t nsrc = 0, pre = 0;
     for (size_t j = 0; j < fresh.size(); ++j) {
       const Active& a = fresh[j];
-      s->h_qnew[j] = QNew{a.base, a.n, a.rq.op, a.slot, nsrc, 1, pre, 0};
-      s->h_srcs[nsrc++] = a.rq.src;
+      hq[j] = QNew{a.base, a.n, a.rq.op, a.slot, nsrc, 1, pre, 0};
+      hs[nsrc++] = a.rq.src;
       pre += a.n;
     }
     AdmitParams ap{};
@@ -518,6 +549,7 @@ bool server_step(irgl_server* s) {
     ap.state = s->state;
     ap.ds = s->ds;
     ap.qlast = s->qlast;
+    ap.qfirst = s->qfirst;
     ap.items[0] = s->items[0];
     ap.items[1] = s->items[1];
     ap.cap = static_cast<uint32_t>(s->arena_n);
@@ -525,137 +557,175 @@ bool server_step(irgl_server* s) {
     ap.st = s->st;
     ap.blim = s->blim;
     ap.delta = s->blim ? s->t.delta : 0u;
-    e = cudaMemcpyAsync(s->qnew, s->h_qnew, sizeof(QNew) * fresh.size(), cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s->srcs, s->h_srcs, sizeof(uint32_t) * nsrc, cudaMemcpyHostToDevice, s->stream);
+    e = cudaMemcpyAsync(s->qnew, hq, sizeof(QNew) * fresh.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->srcs, hs, sizeof(uint32_t) * nsrc, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = launch_admit(ap, static_cast<uint32_t>(s->ctx->sm_count) * 4, s->stream);
     for (auto& a : fresh) s->active.push_back(a);
     std::sort(s->active.begin(), s->active.end(), [](const Active& x, const Active& y) { return x.base < y.base; });
   }
-  // descriptor table of every active query, sorted by base
+  // one epoch over every active query, sorted by base
   const uint32_t nq = static_cast<uint32_t>(s->active.size());
-  for (uint32_t i = 0; i < nq; ++i) {
-    const Active& a = s->active[i];
-    s->h_desc[i] = QDesc{a.rq.g->row_ptr, a.rq.g->col, a.rq.g->w, a.n, a.rq.op, a.base, a.slot};
-    s->h_sbases[i] = a.base;
-  }
-  if (e == cudaSuccess && nq)
-    e = cudaMemcpyAsync(s->desc, s->h_desc, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, s->stream);
-  if (e == cudaSuccess && nq)
-    e = cudaMemcpyAsync(s->sbases, s->h_sbases, sizeof(uint32_t) * nq, cudaMemcpyHostToDevice, s->stream);
-  // one epoch
-  BParams bp{};
-  bp.desc = s->desc;
-  bp.sbases = s->sbases;
-  bp.nq = nq;
-  bp.state = s->state;
-  bp.stamp = s->stamp;
-  bp.ds = s->ds;
-  bp.qlast = s->qlast;
-  bp.items[0] = s->items[0];
-  bp.items[1] = s->items[1];
-  bp.cap = static_cast<uint32_t>(s->arena_n);
-  bp.cont = s->cont;
-  bp.st = s->st;
-  bp.tn = Tune{s->t.warp_thresh, s->t.cta_thresh, s->t.chunk};
-  bp.max_rounds = s->cfg.epoch_rounds;
-  bp.rounds_cap_is_error = 0;
-  bp.timeout_ns = 2000000000ull;
-  bp.big = (s->t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{s->big_e, s->big_off, s->big_cap};
-  bp.delta = s->blim ? s->t.delta : 0u;
-  bp.blim = s->blim;
-  bp.far_items[0] = s->far_items[0];
-  bp.far_items[1] = s->far_items[1];
-  bp.far_cap = s->blim ? static_cast<uint32_t>(s->arena_n) : 0u;
-  bp.far_stamp = s->far_stamp;
-  if (e == cudaSuccess && nq) e = cudaEventRecord(s->ev[0], s->stream);
-  if (e == cudaSuccess && nq) e = launch_batch_iterate(s->t.cta_size, s->grid, bp, s->stream);
-  if (e == cudaSuccess && nq) e = cudaEventRecord(s->ev[1], s->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->st_host, s->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess && nq) e = cudaMemcpyAsync(s->h_qlast, s->qlast, sizeof(uint32_t) * max_slots,
-                                                  cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  if (e != cudaSuccess || s->st_host->err != DERR_NONE) {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->fatal = e != cudaSuccess ? IRGL_ERR_CUDA
-                                : (s->st_host->err == DERR_WL_OVERFLOW ? IRGL_ERR_WL_OVERFLOW : IRGL_ERR_BARRIER_TIMEOUT);
-    s->stop = true;
-    s->cv_done.notify_all();
-    return false;
-  }
-  const uint32_t rounds = s->st_host->rounds;
-  float kms = 0.f;
-  if (nq && cudaEventElapsedTime(&kms, s->ev[0], s->ev[1]) == cudaSuccess) {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->kernel_s += kms * 1e-3;
-  }
-  const uint32_t last_ep = s->st_host->epoch - 1;  // round id of the epoch's last round
-  // finished queries: no push in the last round
-  std::vector<Active> keep, fin;
-  for (auto& a : s->active) {
-    ++a.epochs;
-    if (nq == 0 || s->h_qlast[a.slot] < last_ep || rounds == 0) fin.push_back(a);
-    else keep.push_back(a);
-  }
-  // result sink for queries without a caller buffer (only this thread touches it)
-  uint64_t need = 0;
-  for (auto& a : fin)
-    if (!a.rq.host_out) need = std::max<uint64_t>(need, a.n);
-  if (e == cudaSuccess) e = ensure_scratch(s, need);
-  // every finished query's result and reached edges in one kernel; the result
-  // copies run on the copy stream while the next epochs compute, and the
-  // queries are published (slots and arena released) once they have landed
-  if (!fin.empty() && e == cudaSuccess) {
-    if (s->ring_free.empty()) retire_pending(s, true);  // at most kRing epochs in flight
-    Pending pd;
-    pd.ring = s->ring_free.back();
-    s->ring_free.pop_back();
-    pd.h_edges = s->h_edge_ring + static_cast<size_t>(pd.ring) * max_slots;
-    pd.ev = s->ring_ev[pd.ring];
-    uint64_t total = 0;
-    for (size_t k = 0; k < fin.size(); ++k) {
-      const Active& a = fin[k];
-      s->h_fin[k] = FinDesc{a.rq.g->row_ptr, a.base, a.n, static_cast<uint32_t>(total), a.slot};
-      total += a.n;
-      pd.rounds.push_back(s->h_qlast[a.slot] - a.ep_admit + 2);
+  if (nq && e == cudaSuccess) {
+    QDesc* hd = s->h_desc + static_cast<size_t>(p) * S;
+    uint32_t* hb = s->h_sbases + static_cast<size_t>(p) * S;
+    QDesc* dd = s->desc + static_cast<size_t>(p) * S;
+    uint32_t* db = s->sbases + static_cast<size_t>(p) * S;
+    for (uint32_t i = 0; i < nq; ++i) {
+      const Active& a = s->active[i];
+      hd[i] = QDesc{a.rq.g->row_ptr, a.rq.g->col, a.rq.g->w, a.n, a.rq.op, a.base, a.slot};
+      hb[i] = a.base;
     }
-    e = cudaMemcpyAsync(s->fin, s->h_fin, sizeof(FinDesc) * fin.size(), cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess && s->cfg.count_edges)
-      e = cudaMemsetAsync(s->edge_cnt, 0, sizeof(unsigned long long) * max_slots, s->stream);
-    if (e == cudaSuccess && total) {
-      k_finish<<<static_cast<uint32_t>(s->ctx->sm_count) * 4, 256, 0, s->stream>>>(
-          s->fin, static_cast<uint32_t>(fin.size()), static_cast<uint32_t>(total), s->ds, s->state, s->edge_cnt,
-          s->cfg.count_edges ? 1 : 0);
-      e = cudaGetLastError();
+    e = cudaMemcpyAsync(dd, hd, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(db, hb, sizeof(uint32_t) * nq, cudaMemcpyHostToDevice, s->stream);
+    BParams bp{};
+    bp.desc = dd;
+    bp.sbases = db;
+    bp.nq = nq;
+    bp.state = s->state;
+    bp.stamp = s->stamp;
+    bp.ds = s->ds;
+    bp.qlast = s->qlast;
+    bp.items[0] = s->items[0];
+    bp.items[1] = s->items[1];
+    bp.cap = static_cast<uint32_t>(s->arena_n);
+    bp.cont = s->cont;
+    bp.st = s->st;
+    bp.tn = Tune{s->t.warp_thresh, s->t.cta_thresh, s->t.chunk};
+    bp.max_rounds = s->cfg.epoch_rounds;
+    bp.rounds_cap_is_error = 0;
+    bp.timeout_ns = 2000000000ull;
+    bp.big = (s->t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{s->big_e, s->big_off, s->big_cap};
+    bp.delta = s->blim ? s->t.delta : 0u;
+    bp.blim = s->blim;
+    bp.far_items[0] = s->far_items[0];
+    bp.far_items[1] = s->far_items[1];
+    bp.far_cap = s->blim ? static_cast<uint32_t>(s->arena_n) : 0u;
+    bp.far_stamp = s->far_stamp;
+    if (e == cudaSuccess) e = cudaEventRecord(s->ep_ev[2 * p], s->stream);
+    if (e == cudaSuccess) e = launch_batch_iterate(s->t.cta_size, s->grid, bp, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ep_ev[2 * p + 1], s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->st_host + p, s->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->h_qlast + static_cast<size_t>(p) * S, s->qlast, sizeof(uint32_t) * S,
+                          cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->h_qfirst + static_cast<size_t>(p) * S, s->qfirst, sizeof(uint32_t) * S,
+                          cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->st_ev[p], s->stream);
+    s->rec[p].live = true;
+    s->rec[p].set = s->active;
+    s->par = q;
+  }
+  // read back the previous step's epoch
+  uint32_t rounds = 0;
+  bool read_back = false;
+  if (s->rec[q].live && e == cudaSuccess) {
+    read_back = true;
+    e = cudaEventSynchronize(s->st_ev[q]);
+    const DevStatus& sh = s->st_host[q];
+    if (e != cudaSuccess || sh.err != DERR_NONE) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->fatal = e != cudaSuccess ? IRGL_ERR_CUDA
+                                  : (sh.err == DERR_WL_OVERFLOW ? IRGL_ERR_WL_OVERFLOW : IRGL_ERR_BARRIER_TIMEOUT);
+      s->stop = true;
+      s->cv_done.notify_all();
+      return false;
     }
-    if (e == cudaSuccess && s->cfg.count_edges)
-      e = cudaMemcpyAsync(pd.h_edges, s->edge_cnt, sizeof(unsigned long long) * max_slots, cudaMemcpyDeviceToHost,
-                          s->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy_stream, pd.ev, 0);
-    for (auto& a : fin) {
-      uint32_t* dst = a.rq.host_out ? a.rq.host_out : s->h_scratch;
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dst, s->state + a.base, sizeof(uint32_t) * (size_t)a.n, cudaMemcpyDeviceToHost,
-                            s->copy_stream);
+    rounds = sh.rounds;
+    float kms = 0.f;
+    if (cudaEventElapsedTime(&kms, s->ep_ev[2 * q], s->ep_ev[2 * q + 1]) == cudaSuccess) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->kernel_s += kms * 1e-3;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->copy_stream);
-    pd.fin = std::move(fin);
-    s->pending.push_back(std::move(pd));
+    const uint32_t last_ep = sh.epoch - 1;  // round id of the epoch's last round
+    const uint32_t* hl = s->h_qlast + static_cast<size_t>(q) * S;
+    const uint32_t* hf = s->h_qfirst + static_cast<size_t>(q) * S;
+    // finished queries: no push in the epoch's last round. Only queries still
+    // active count: one already finished by the previous read-back also sat,
+    // inert, in this epoch's set
+    std::vector<uint64_t> live_ticket(S, ~uint64_t{0});
+    for (auto& a : s->active) live_ticket[a.slot] = a.rq.ticket;
+    std::vector<Active> fin;
+    std::vector<char> done_slot(S, 0);
+    for (auto& a : s->rec[q].set) {
+      if (live_ticket[a.slot] != a.rq.ticket) continue;
+      if (hl[a.slot] < last_ep || rounds == 0) {
+        fin.push_back(a);
+        done_slot[a.slot] = 1;
+      }
+    }
+    s->rec[q].live = false;
+    s->rec[q].set.clear();
+    if (!fin.empty()) {
+      std::vector<Active> keep;
+      keep.reserve(s->active.size());
+      for (auto& a : s->active)
+        if (!done_slot[a.slot]) keep.push_back(a);
+      s->active.swap(keep);
+    }
+    // result sink for queries without a caller buffer (only this thread touches it)
+    uint64_t need = 0;
+    for (auto& a : fin)
+      if (!a.rq.host_out) need = std::max<uint64_t>(need, a.n);
+    if (e == cudaSuccess) e = ensure_scratch(s, need);
+    // every finished query's result and reached edges in one kernel (after the
+    // epoch now running: these queries are inert in it); the result copies run
+    // on the copy stream, and the queries are published (slots and arena
+    // released) once they have landed
+    if (!fin.empty() && e == cudaSuccess) {
+      if (s->ring_free.empty()) retire_pending(s, true);  // at most kRing epochs in flight
+      Pending pd;
+      pd.ring = s->ring_free.back();
+      s->ring_free.pop_back();
+      pd.h_edges = s->h_edge_ring + static_cast<size_t>(pd.ring) * S;
+      pd.ev = s->ring_ev[pd.ring];
+      FinDesc* hfd = s->h_fin + static_cast<size_t>(q) * S;
+      uint64_t total = 0;
+      for (size_t k = 0; k < fin.size(); ++k) {
+        const Active& a = fin[k];
+        hfd[k] = FinDesc{a.rq.g->row_ptr, a.base, a.n, static_cast<uint32_t>(total), a.slot};
+        total += a.n;
+        pd.rounds.push_back(hl[a.slot] - hf[a.slot] + 2);
+      }
+      e = cudaMemcpyAsync(s->fin, hfd, sizeof(FinDesc) * fin.size(), cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess && s->cfg.count_edges)
+        e = cudaMemsetAsync(s->edge_cnt, 0, sizeof(unsigned long long) * S, s->stream);
+      if (e == cudaSuccess && total) {
+        k_finish<<<static_cast<uint32_t>(s->ctx->sm_count) * 4, 256, 0, s->stream>>>(
+            s->fin, static_cast<uint32_t>(fin.size()), static_cast<uint32_t>(total), s->ds, s->state, s->edge_cnt,
+            s->cfg.count_edges ? 1 : 0);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess && s->cfg.count_edges)
+        e = cudaMemcpyAsync(pd.h_edges, s->edge_cnt, sizeof(unsigned long long) * S, cudaMemcpyDeviceToHost,
+                            s->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy_stream, pd.ev, 0);
+      for (auto& a : fin) {
+        uint32_t* dst = a.rq.host_out ? a.rq.host_out : s->h_scratch;
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(dst, s->state + a.base, sizeof(uint32_t) * (size_t)a.n, cudaMemcpyDeviceToHost,
+                              s->copy_stream);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->copy_stream);
+      pd.fin = std::move(fin);
+      s->pending.push_back(std::move(pd));
+    }
   }
   const double t_done = now_s();
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    s->epochs += 1;
-    s->rounds_total += rounds;
+    if (read_back) {
+      s->epochs += 1;
+      s->rounds_total += rounds;
+    }
     s->busy_s += t_done - t0;
     if (e != cudaSuccess) {
       s->fatal = IRGL_ERR_CUDA;
       s->stop = true;
       s->cv_done.notify_all();
     }
-    s->active.swap(keep);
   }
   return true;
 }
@@ -668,7 +738,8 @@ void server_loop(irgl_server* s) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->stop) break;
-      if (s->queue.empty() && s->active.empty() && s->solo_q.empty() && s->pending.empty())
+      if (s->queue.empty() && s->active.empty() && s->solo_q.empty() && s->pending.empty() && !s->rec[0].live &&
+          !s->rec[1].live)
         s->cv.wait_for(lk, std::chrono::milliseconds(2));
       if (s->stop) break;
     }
@@ -726,8 +797,10 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   }
   if (e == cudaSuccess) e = cudaEventCreate(&s->ev[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&s->ev[1]);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->ep_ev[i]);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&s->st_ev[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&s->st, sizeof(DevStatus));
-  if (e == cudaSuccess) e = cudaMallocHost(&s->st_host, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaMallocHost(&s->st_host, 2 * sizeof(DevStatus));
   if (e == cudaSuccess) e = cudaMalloc(&s->state, sizeof(uint32_t) * s->arena_n);
   if (e == cudaSuccess) {
     if (packed) e = cudaMalloc(&s->ds, sizeof(unsigned long long) * s->arena_n);
@@ -741,8 +814,9 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   if (nf && e == cudaSuccess) e = cudaMalloc(&s->far_items[1], sizeof(uint32_t) * s->arena_n);
   if (nf && e == cudaSuccess) e = cudaMalloc(&s->far_stamp, sizeof(uint32_t) * s->arena_n);
   if (nf && e == cudaSuccess) e = cudaMalloc(&s->blim, sizeof(uint32_t) * S);
-  if (e == cudaSuccess) e = cudaMalloc(&s->desc, sizeof(QDesc) * S);
-  if (e == cudaSuccess) e = cudaMalloc(&s->sbases, sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMalloc(&s->desc, 2 * sizeof(QDesc) * S);
+  if (e == cudaSuccess) e = cudaMalloc(&s->sbases, 2 * sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMalloc(&s->qfirst, sizeof(uint32_t) * S);
   if (e == cudaSuccess) e = cudaMalloc(&s->qnew, sizeof(QNew) * S);
   if (e == cudaSuccess) e = cudaMalloc(&s->srcs, sizeof(uint32_t) * S);
   if (e == cudaSuccess) e = cudaMalloc(&s->edge_cnt, sizeof(unsigned long long) * S);
@@ -751,13 +825,14 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
     s->big_cap = big_capacity(s->arena_n);
     e = alloc_big(s->big_cap, &s->big_e, &s->big_off);
   }
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_desc, sizeof(QDesc) * S);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_sbases, sizeof(uint32_t) * S);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_qnew, sizeof(QNew) * S);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_srcs, sizeof(uint32_t) * S);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_qlast, sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_desc, 2 * sizeof(QDesc) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_sbases, 2 * sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_qnew, 2 * sizeof(QNew) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_srcs, 2 * sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_qlast, 2 * sizeof(uint32_t) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_qfirst, 2 * sizeof(uint32_t) * S);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_edges, sizeof(unsigned long long) * S);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_fin, sizeof(FinDesc) * S);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_fin, 2 * sizeof(FinDesc) * S);
   if (e != cudaSuccess) {
     server_free(s);
     delete s;
