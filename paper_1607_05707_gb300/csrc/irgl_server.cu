@@ -72,7 +72,6 @@ struct Active {
   uint32_t slot = 0;
   uint32_t base = 0;
   uint32_t n = 0;
-  uint32_t epochs = 0;
 };
 
 // An epoch launched and not yet read back: the queries it ran over.
@@ -252,7 +251,6 @@ struct irgl_server {
   uint32_t* h_srcs = nullptr;
   uint32_t* h_qlast = nullptr;
   uint32_t* h_qfirst = nullptr;
-  unsigned long long* h_edges = nullptr;
   FinDesc* h_fin = nullptr;
   uint32_t* qfirst = nullptr;  // device, per slot: the round id the query was admitted at
   // epochs in flight: epoch k+1 is launched before epoch k is read back
@@ -323,7 +321,6 @@ void server_free(irgl_server* s) {
   if (s->h_qnew) cudaFreeHost(s->h_qnew);
   if (s->h_srcs) cudaFreeHost(s->h_srcs);
   if (s->h_qlast) cudaFreeHost(s->h_qlast);
-  if (s->h_edges) cudaFreeHost(s->h_edges);
   if (s->h_fin) cudaFreeHost(s->h_fin);
   if (s->h_scratch) cudaFreeHost(s->h_scratch);
   if (s->ev[0]) cudaEventDestroy(s->ev[0]);
@@ -831,7 +828,6 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_srcs, 2 * sizeof(uint32_t) * S);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_qlast, 2 * sizeof(uint32_t) * S);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_qfirst, 2 * sizeof(uint32_t) * S);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_edges, sizeof(unsigned long long) * S);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_fin, 2 * sizeof(FinDesc) * S);
   if (e != cudaSuccess) {
     server_free(s);
