@@ -350,7 +350,10 @@ irgl_status irgl_batch_autotune(irgl_batch* b, uint32_t reps, irgl_tuning* best,
  * epochs of the batched persistent
  * kernel (at most epoch_rounds rounds over every active query), and retires
  * the queries that finished: their result is copied to the caller's host
- * buffer (if one was given), and their memory and slot are reused. Queries
+ * buffer (if one was given) on a second stream while later epochs run, and the
+ * query is reported done (irgl_server_poll) once its copy has landed; then its
+ * memory and slot are reused. The worker keeps two epochs in flight (it reads
+ * one back while the next runs). Queries
  * that arrive while others run join the next epoch; their work overlaps on
  * the device. Submission is thread-safe. */
 typedef struct {
