@@ -234,3 +234,49 @@ def test_trace_records_rounds(ctx):
     np.testing.assert_array_equal(a[1:], np.minimum(r + 1, 127 - r))
     assert o[-1] == 0
     dg.close()
+
+
+@pytest.mark.parametrize("delta", [0, 32])
+def test_batch_config_sample_near_far(ctx, delta):
+    """A sample of the 256-instance R-MAT workload batched with and without per-query near-far."""
+    from paper_1607_05707_gb300.api import Batch
+
+    inst = inputs.workload_batch(count=16)
+    graphs = [ctx.load(g, validate=False) for g, _ in inst]
+    b = Batch(ctx, 16)
+    for (g, s), dg in zip(inst, graphs):
+        b.add("sssp", dg, s)
+    b.prepare(dict(delta=delta))
+    b.run()
+    for q, (g, s) in enumerate(inst):
+        np.testing.assert_array_equal(b.result(q)[0], oracle.sssp(g.n, g.row_ptr, g.col, g.w, s), err_msg=f"{q}")
+    b.close()
+    for dg in graphs:
+        dg.close()
+
+
+@pytest.mark.parametrize("delta", [0, 512])
+def test_grid_batch_matches_oracle(ctx, delta):
+    """The serving-like grid batch (BFS and SSSP queries sharing a few weighted grids), smaller sides."""
+    from paper_1607_05707_gb300.api import Batch
+
+    inst = inputs.workload_grid_batch(count=12, graphs=4, lo=64, hi=220)
+    loaded = {}
+    for g, _, _ in inst:
+        if id(g) not in loaded:
+            loaded[id(g)] = ctx.load(g)
+    b = Batch(ctx, 16)
+    for g, s, k in inst:
+        b.add(k, loaded[id(g)], s)
+    b.prepare(dict(delta=delta))
+    for rep in range(2):
+        b.run()
+        for q, (g, s, k) in enumerate(inst):
+            got, rounds = b.result(q)
+            want = oracle.run(k, g, s)
+            np.testing.assert_array_equal(got, want, err_msg=f"query {q} ({k}) delta {delta} rep {rep}")
+            if k == "bfs":
+                assert rounds == int(want[want != INF].max()) + 1
+    b.close()
+    for dg in loaded.values():
+        dg.close()
