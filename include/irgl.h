@@ -407,7 +407,8 @@ irgl_status irgl_server_destroy(irgl_server* s);
  * latency-critical loop that cannot take the implicit device synchronisation
  * a cudaMalloc may bring. It runs the persistent BFS Iterate from one source
  * and calls no cudaMalloc, cudaFree or other allocating routine.
- *   device, cuda_stream: the GPU and the stream (cudaStream_t as void*) to run on
+ *   device, cuda_stream: the GPU and the stream (cudaStream_t as void*) to run on;
+ *                        a non-null stream of another device is IRGL_ERR_INVALID_ARG
  *   n, m, row_ptr, col:  the caller's device CSR (as irgl_csr_load; col 16-byte aligned)
  *   src:                 source vertex, < n
  *   level:               caller's device array of n uint32 levels (INF = unreachable)

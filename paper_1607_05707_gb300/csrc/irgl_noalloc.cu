@@ -15,6 +15,7 @@
 // device uses the same array and it keeps the previous call's contents, so each
 // call clears the counters that must start at zero; calls whose GPU work
 // overlaps (other streams or threads) race on the array and give wrong results.
+// A non-null stream must belong to `device` (checked: IRGL_ERR_INVALID_ARG).
 // The first call on a device looks up the array's device address (with that
 // device current) and caches it; make that first call before any stream
 // capture.
@@ -30,7 +31,7 @@ namespace irgl {
 namespace {
 
 constexpr uint32_t kNoAllocMaxN = 1u << 20;    // vertices
-constexpr uint32_t kNoAllocBigCap = 1u << 16;  // big-list entries; longer rounds fall back to the CTA bin
+constexpr uint32_t kNoAllocBigCap = 1u << 16;  // big-list entries; long lists beyond it go to the warp bin
 constexpr int kNoAllocCta = 256;
 constexpr int kMaxDevices = 64;
 
@@ -98,11 +99,19 @@ extern "C" irgl_status irgl_bfs_noalloc(int device, void* cuda_stream, uint32_t 
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
   if (device < 0 || device >= ndev || device >= kMaxDevices)
     return fail(IRGL_ERR_INVALID_ARG, "device %d out of range", device);
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  if (stream != nullptr) {
+    // the scratch address below is the one on `device`: a stream of another GPU would
+    // send the launch to that GPU's copy of the array through the wrong address
+    int sdev = -1;
+    e = cudaStreamGetDevice(stream, &sdev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamGetDevice");
+    if (sdev != device) return fail(IRGL_ERR_INVALID_ARG, "cuda_stream belongs to device %d, not %d", sdev, device);
+  }
   DeviceSetup d;
   irgl_status s = setup_device(device, &d);
   if (s != IRGL_OK) return s;
   DeviceGuard guard(device);
-  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   NoAllocScratch* sc = d.scratch;
 
   // what must start at zero: the whole status block (barrier, tails, grabs, big list, error)

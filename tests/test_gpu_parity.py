@@ -365,7 +365,7 @@ def test_errors_and_recovery(ctx):
 
 
 def test_big_list_overflow_falls_back(ctx):
-    # a big list of 3 entries: further long lists take the CTA-bin path in the same round
+    # a big list of 3 entries: further long lists take the warp-bin path in the same round
     g = inputs.rmat(14, 16, seed=61, weights=True)
     dg = ctx.load(g)
     s = inputs.sources(g, 1, seed=62)

@@ -167,3 +167,52 @@ def test_server_large_queries_run_alone(env):
     n_solo = sum(1 for _, gi, _ in qs if graphs[gi].n >= 16384)
     assert st["completed"] == len(qs) and st["solo"] == n_solo and 0 < n_solo < len(qs)
     srv.close()
+
+
+def test_server_serving_bench_settings_match_oracle():
+    """The serving workload's own settings on a reduced mix: direction-optimising BFS
+    (tuning flag 2) for the R-MAT graph's queries, which run alone on a graph loaded
+    with in-edges; per-query near-far at delta 512 for the SSSP queries; 32 rounds per
+    epoch; 512 slots; CTAs of 1024; grids up to side 1024 in the batch arena. A few
+    hundred queries arrive from a feeder thread at about 2000 per second, so late
+    arrivals join epochs already running. Every result is compared with the oracle's
+    element by element."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_05707_gb300.api import Context, Server
+
+    ctx = Context(0, torch.cuda.Stream())
+    graphs = [inputs.rmat(21, 16, seed=1105, weights=True)]
+    graphs += [inputs.mesh(s, s, seed=1105000 + s, weights=True) for s in (1024, 640, 300, 256)]
+    dgs = [ctx.load(g, validate=False, in_edges=(i == 0)) for i, g in enumerate(graphs)]
+    rng = np.random.default_rng(1106)
+    nq = 256
+    # the R-MAT graph takes a small share so the serial oracle stays within seconds
+    gis = np.where(np.arange(nq) % 16 == 0, 0, rng.integers(1, len(graphs), size=nq))
+    kinds = np.where(rng.random(nq) < 0.7, "bfs", "sssp")
+    srcs = [int(inputs.sources(graphs[gi], 1, seed=1107000 + i)[0]) for i, gi in enumerate(gis)]
+    gaps = rng.exponential(1.0 / 2000.0, size=nq)
+    srv = Server(ctx, arena_bytes=8 << 30, max_slots=512, epoch_rounds=32, count_edges=True,
+                 tuning={"delta": 512, "flags": 2, "cta_size": 1024}, solo_min_n=(1 << 20) + 1)
+    bufs = [np.empty(graphs[gi].n, dtype=np.uint32) for gi in gis]
+    tickets = [None] * nq
+
+    def feeder():
+        for i in range(nq):
+            time.sleep(float(gaps[i]))
+            tickets[i] = srv.submit(str(kinds[i]), dgs[gis[i]], srcs[i], bufs[i])
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    srv.drain(600)
+    st = srv.stats()
+    n_solo = int((gis == 0).sum())
+    assert st["completed"] == nq and st["rejected"] == 0 and st["solo"] == n_solo
+    for i in range(nq):
+        _check(graphs, (str(kinds[i]), int(gis[i]), srcs[i]), bufs[i], srv.poll(tickets[i]))
+    srv.close()
+    for d in dgs:
+        d.close()
+    ctx.close()
