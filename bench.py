@@ -70,6 +70,15 @@ def parse_args():
     ap.add_argument("--epoch-rounds", type=int, default=32, help="serve: rounds per epoch")
     ap.add_argument("--arena-gb", type=float, default=0.0, help="serve: device arena budget (0: 40% of free HBM)")
     ap.add_argument("--verify", type=int, default=32, help="serve: queries checked against the oracle")
+    ap.add_argument("--per-launch-sample", type=int, default=160,
+                    help="serve: served queries rerun one persistent launch each for the per-launch comparison")
+    ap.add_argument("--sub-serve-duration", type=float, default=10.0,
+                    help="rmat20: arrival window (s) of the serving sub-record")
+    ap.add_argument("--autotune", choices=["auto", "on", "off"], default="auto",
+                    help="single-query workloads: pick each kernel's tuning with irgl_autotune before timing "
+                         "(auto: on for grid64, off otherwise)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="rmat20: leave out the batch and serving sub-records of the default line")
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (rmat20 workload)")
     ap.add_argument("--mesh-side", type=int, default=4096)
     ap.add_argument("--cc", choices=["label", "jump"], default="label",
@@ -85,11 +94,16 @@ def parse_args():
     ap.add_argument("--tuning", type=str, default="", help="JSON irgl_tuning overrides")
     ap.add_argument("--trace", action="store_true", help="print a per-round trace of one query per kernel to stderr")
     ap.add_argument("--diropt", action="store_true",
-                    help="BFS direction-optimising (bottom-up rounds on large frontiers; loads the in-edge CSR)")
+                    help="BFS direction-optimising (bottom-up rounds on large frontiers; loads the in-edge CSR); "
+                         "the default on the R-MAT workload")
+    ap.add_argument("--no-diropt", action="store_true",
+                    help="rmat20: time the top-down-only BFS in the headline instead")
     ap.add_argument("--local", type=int, default=-1,
                     help="CTA-local sub-rounds for persistent BFS/SSSP (0..15; default: 15 on the high-diameter "
                          "grid64 and mesh workloads, 0 on R-MAT, as the autotuner picks them)")
     args = ap.parse_args()
+    if args.workload == "rmat20" and not args.no_diropt:
+        args.diropt = True
     if args.steps is None:
         args.steps = 1000 if args.workload == "grid64" else 16
     return args
@@ -416,6 +430,14 @@ def run_gpu(args, world, rank, local):
         if k == "cc" and args.cc_delta and "delta" not in t:
             t["delta"] = args.cc_delta
         ktune[k] = t or None
+    autotuned = {}
+    if args.autotune == "on" or (args.autotune == "auto" and args.workload == "grid64" and not tuning):
+        # the search runs before the timed region; its choice is recorded in the line's config
+        for k in kernels:
+            t0 = time.perf_counter()
+            best, ms = ctx.autotune(k, dg, None if k.startswith("cc") else [int(srcs[0])], reps=5)
+            ktune[k] = best
+            autotuned[k] = {"search_s": round(time.perf_counter() - t0, 1), "median_ms": round(ms, 4)}
     wls = []
     for s in srcs:
         wl = ctx.worklist(4)
@@ -461,9 +483,12 @@ def run_gpu(args, world, rank, local):
             ctx.iterate_async(k, dg, init(k, used[0]), out[k], tuning=ktune[k])
             st = ctx.sync()
             t, a, o = C.irgl_trace_read(ctx.handle)
-            print(f"# trace {k} source {srcs[used[0]]}: rounds={st['rounds']} total_us={(int(t[-1]) - int(t[0])) / 1e3:.1f}",
-                  file=sys.stderr)
+            print(f"# trace {k} source {srcs[used[0]]}: rounds={st['rounds']} total_us={(int(t[-1]) - int(t[0])) / 1e3:.1f}"
+                  f" prologue_us={int(o[0]) / 1e3:.2f}", file=sys.stderr)
             for r in range(1, len(t)):
+                if int(a[r]) == INF and int(o[r]) == INF:
+                    print(f"#  epilogue us {(int(t[r]) - int(t[r - 1])) / 1e3:9.2f}", file=sys.stderr)
+                    continue
                 print(f"#  round {r - 1:5d} us {(int(t[r]) - int(t[r - 1])) / 1e3:9.2f} in {int(a[r]):9d} out {int(o[r]):9d}",
                       file=sys.stderr)
         C.irgl_trace_enable(ctx.handle, 0)
@@ -517,6 +542,42 @@ def run_gpu(args, world, rank, local):
                 "by_kernel": {k: {kk: (round(v, 4) if isinstance(v, float) else v) for kk, v in d.items()}
                               for k, d in per_kernel.items()}}
 
+    # BFS in the other form (top-down only when the headline is direction-optimising, and the
+    # reverse), event-timed on the same sources outside the headline's timed region
+    bfs_other = None
+    if "bfs" in kernels and args.workload == "rmat20":
+        t_other = dict(ktune["bfs"] or {})
+        t_other["flags"] = int(t_other.get("flags", 0)) ^ 2
+        t_other = t_other if any(t_other.values()) else None
+        if not args.diropt:
+            dg_other = ctx.load(g, validate=False, in_edges=True)
+        else:
+            dg_other = dg
+        tt, bb, ee, nn = 0.0, 0, 0, 0
+        for i in range(args.steps):
+            j = used[i]
+            with torch.cuda.stream(stream):
+                flush.fill_(i)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.iterate_async("bfs", dg_other, wls[j], out["bfs"], tuning=t_other)
+            e1.record(stream)
+            ctx.sync()
+            if i < max(1, args.warmup // 2):
+                continue  # first uses of the other form
+            R, mR = counts[(j, "bfs")]
+            tt += e0.elapsed_time(e1) * 1e-3
+            bb += alg_bytes("bfs", g.n, R, mR)
+            ee += mR
+            nn += 1
+        if nn:
+            bfs_other = {"form": "top-down only" if args.diropt else "direction-optimising",
+                         "us_per_launch": round(1e6 * tt / nn, 2), "gteps": round(ee / tt / 1e9, 4),
+                         "roofline_frac": round(bb / tt / 1e9 / hbm, 4), "launches": nn}
+        if dg_other is not dg:
+            dg_other.close()
+
     # e2e through the C-ABI with pinned host buffers (host wall clock per call, copies inside)
     host_out = torch.empty(g.n, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
     s = torch.empty(1, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
@@ -547,15 +608,46 @@ def run_gpu(args, world, rank, local):
             t0 = time.perf_counter()
             _, st = ctx.iterate("bfs", dg, wls[j], out["bfs"], mode="per_launch", tuning=ktune["bfs"])
             t_pl.append(time.perf_counter() - t0)
-        t_pers = [t for (t, _, _), jj in zip(rec["bfs"], used) if jj == j]
-        outlining = {"kernel": "bfs", "rounds": st["rounds"], "per_launch_us": round(1e6 * min(t_pl), 1),
-                     "per_launch_launches": st["launches"],
+        if args.diropt:
+            # the per-launch form runs top-down rounds only: compare it with the persistent top-down form
+            t_plain = dict(ktune["bfs"] or {})
+            t_plain["flags"] = int(t_plain.get("flags", 0)) & ~2
+            t_pers = []
+            for rep_i in range(4):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.iterate_async("bfs", dg, wls[j], out["bfs"], tuning=t_plain if any(t_plain.values()) else None)
+                e1.record(stream)
+                ctx.sync()
+                if rep_i:
+                    t_pers.append(e0.elapsed_time(e1) * 1e-3)
+        else:
+            t_pers = [t for (t, _, _), jj in zip(rec["bfs"], used) if jj == j]
+        outlining = {"kernel": "bfs (top-down rounds in both forms)", "rounds": st["rounds"],
+                     "per_launch_us": round(1e6 * min(t_pl), 1), "per_launch_launches": st["launches"],
                      "persistent_us": round(1e6 * statistics.median(t_pers), 1),
                      "speedup": round(min(t_pl) / statistics.median(t_pers), 2)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(g, srcs_all, kernels, args.cpu_budget)
+
+    # the other parts of the metric on the same GPU, in the same run: the 256-instance batch
+    # (batched vs one launch per query) and a serving window (served vs one launch per query,
+    # p50/p99 latency)
+    extras = {}
+    if args.workload == "rmat20" and args.scale == 20 and not args.no_extras:
+        import copy
+
+        sub = copy.copy(args)
+        sub.tuning, sub.steps, sub.warmup = "", min(args.steps, 10), 3
+        sub.instances, sub.batch_set, sub.no_autotune, sub.wave_mb = 256, "rmat", False, None
+        extras["batch"] = run_batch(sub, world, rank, local, embedded=True)
+        sub = copy.copy(args)
+        sub.tuning, sub.rate, sub.duration, sub.verify = "", 2000.0, args.sub_serve_duration, 16
+        sub.serve_scale, sub.slots, sub.epoch_rounds, sub.arena_gb = 24, 512, 32, 0.0
+        extras["serve"] = run_serve(sub, world, rank, local, embedded=True)
 
     if rank == 0:
         launches_per_step = len(kernels)  # one persistent Iterate launch per query (the L2 flush fill is torch's)
@@ -568,7 +660,8 @@ def run_gpu(args, world, rank, local):
                            + (f", {local_k} CTA-local sub-rounds per round" if local_k else ""),
                            parallelism=f"replicas x{world} (queries sharded, no collective)",
                            l2="flushed between steps (512 MB write, outside the events)",
-                           tuning={k: {**ctx.default_tuning, **(ktune[k] or {})} for k in kernels}),
+                           tuning={k: {**ctx.default_tuning, **(ktune[k] or {})} for k in kernels},
+                           autotuned=autotuned or None),
             "e2e": {"value": round(e2e_val, 4), "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(kernels),
                     "d2h_bytes_per_step": 4 * g.n * len(kernels)},
             "gpu_launches": launches_per_step * args.steps,
@@ -577,6 +670,10 @@ def run_gpu(args, world, rank, local):
             "clocks": clk,
             "wall_s_timed_region": round(t_wall, 4),
             "outlining": outlining,
+            "rmat20_bfs_roofline_frac": (round(per_kernel["bfs"]["achieved_gbs"] / hbm, 4)
+                                         if "bfs" in per_kernel and args.workload == "rmat20" else None),
+            "bfs_other_form": bfs_other,
+            **extras,
         }
         print(json.dumps(line), flush=True)
     for wl in wls:
@@ -587,9 +684,10 @@ def run_gpu(args, world, rank, local):
 
 # ----------------------------------------------------------------------------- batched workload
 
-def run_batch(args, world, rank, local):
+def run_batch(args, world, rank, local, embedded=False):
     """256 independent SSSP instances (R-MAT scale 10..18, edge factor 8, 1-4 sources) in one
-    CUDA-graph-replayed persistent launch, against the same queries run one launch each."""
+    CUDA-graph-replayed persistent launch, against the same queries run one launch each.
+    embedded: return a compact record (rank 0) for the default bench line instead of printing."""
     import torch
 
     from paper_1607_05707_gb300 import irgl as C
@@ -690,7 +788,7 @@ def run_batch(args, world, rank, local):
     t_e2e = max_over_ranks(statistics.median(t_e2e_all), world, dev)
     e2e = sum_over_ranks(edges, world, dev) / t_e2e / 1e9
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not embedded:
         import oracle
 
         tt, ee, nq = 0.0, 0, 0
@@ -706,6 +804,27 @@ def run_batch(args, world, rank, local):
                "sample": f"first {nq} instances (serial BFS / Dijkstra), {tt:.1f} s on {platform.machine()} host"}
     hbm, peak_src = peaks()
     nbytes = sum(alg_bytes(k, g.n, int((b.result(q)[0] != INF).sum()), m) for q, ((g, _, k), m) in enumerate(zip(inst, mR)))
+    if embedded:
+        b.close()
+        for wl in wls:
+            wl.close()
+        for dg in loaded.values():
+            dg.close()
+        ctx.close()
+        if rank != 0:
+            return None
+        return {
+            "workload": (f"batch{len(inst_all)}: SSSP instances, R-MAT scale U{{10..18}}, edge factor 8, 1-4 sources, "
+                         f"w in [1,100]; one CUDA-graph replay of {info['waves']} wave(s)"),
+            "gteps": round(value, 4), "ms_per_run": round(1e3 * t_batch, 4), "steps": args.steps,
+            "per_launch_gteps": round(seq_dev_gteps, 4), "batched_vs_per_launch": round(value / seq_dev_gteps, 3),
+            "clock": "device (CUDA events) for both forms; per-launch = the same instances, one persistent launch each",
+            "per_launch_gteps_wall": round(seq_gteps, 4),
+            "e2e_gteps": round(e2e, 4),
+            "roofline_frac": round(nbytes / t_batch / 1e9 / hbm, 4),
+            "verified": "every instance's batched result equals its one-launch result",
+            "tuning": {**ctx.default_tuning, **(tuning or {})}, "autotuned": autotuned, "clocks": clk,
+        }
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
@@ -742,9 +861,12 @@ def inputs_workload_batch(count):
 
 # ----------------------------------------------------------------------------- serving workload
 
-def run_serve(args, world, rank, local):
+def run_serve(args, world, rank, local, embedded=False):
     """Poisson arrivals of BFS (70%) / SSSP (30%) queries with uniform sources against one R-MAT
-    graph and 32 grids of side U[256, 2048], served by the continuous-batching server."""
+    graph and 32 grids of side U[256, 2048], served by the continuous-batching server. Then a
+    sample of the same queries runs one persistent launch per query (host waits for each), the
+    one-query-per-launch form the served throughput is compared with (host wall clock for both).
+    embedded: return a compact record (rank 0) for the default bench line instead of printing."""
     import threading
 
     import torch
@@ -760,9 +882,11 @@ def run_serve(args, world, rank, local):
     graphs += [inputs.mesh(int(sd), int(sd), seed=1005000 + i, weights=True) for i, sd in enumerate(sides)]
     # per-query near-far for the SSSP queries (delta 512: measured 3x the plain rounds' GTEPS
     # on this mix, where grid SSSP re-relaxes each edge about 40 times); the R-MAT graph's BFS
-    # queries run alone and direction-optimising (in-edges loaded: 2.8 -> 1.5 ms at scale 24);
-    # CTAs of 1024 (10 s of arrivals: 26.8 GTEPS, p50 340 ms, against 26.0 and 564 ms with 128)
-    tuning = json.loads(args.tuning) if args.tuning else {"delta": 512, "flags": 2, "cta_size": 1024}
+    # queries run alone and direction-optimising (flag 2, in-edges loaded); 15 CTA-local
+    # sub-rounds per batched round, so a grid query needs far fewer global rounds than levels
+    # (10 s of arrivals: p50 126 -> 67 ms, p99 372 -> 243 ms at the same 27.7 GTEPS); CTAs of
+    # 1024 (26.8 GTEPS, p50 340 ms, against 26.0 and 564 ms with 128, before sub-rounds)
+    tuning = json.loads(args.tuning) if args.tuning else {"delta": 512, "flags": 2 | (15 << 8), "cta_size": 1024}
     ctx = Context(local, torch.cuda.Stream(device=dev))
     dgs = [ctx.load(g, validate=False, in_edges=(i == 0)) for i, g in enumerate(graphs)]
     arrivals = inputs.poisson_arrivals(args.rate, args.duration, seed=2005 + rank)
@@ -815,6 +939,61 @@ def run_serve(args, world, rank, local):
         bad += int(not np.array_equal(want, bufs[i]))
     if bad:
         raise RuntimeError(f"{bad} of {len(verify)} sampled served queries differ from the oracle")
+    # one-query-per-launch form on a sample of the served queries: each query alone, one persistent
+    # launch, host waiting for its status, with the best single-query settings per graph class
+    # (R-MAT: direction-optimising BFS; grids: CTA-local sub-rounds)
+    pl_idx = sorted(rng.choice(nq, size=min(args.per_launch_sample, nq), replace=False).tolist())
+    wl = ctx.worklist(4)
+    pl_out = ctx.state(max(g.n for g in graphs))
+
+    def pl_tuning(i):
+        if gi[i] == 0:
+            return {"flags": 2} if kinds[i] == "bfs" else None
+        return {"flags": 15 << 8}
+
+    for i in pl_idx[:4]:  # untimed first use of each setting
+        wl.clear()
+        wl.push([int(srcs[i])])
+        ctx.iterate(str(kinds[i]), dgs[gi[i]], wl, pl_out, tuning=pl_tuning(i))
+    pl_wall, pl_dev, pl_edges = 0.0, 0.0, 0
+    for i in pl_idx:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        wl.clear()
+        wl.push([int(srcs[i])])
+        e0.record(ctx.stream)
+        ctx.iterate_async(str(kinds[i]), dgs[gi[i]], wl, pl_out, tuning=pl_tuning(i))
+        e1.record(ctx.stream)
+        ctx.sync()
+        pl_wall += time.perf_counter() - t1
+        pl_dev += e0.elapsed_time(e1) * 1e-3
+        pl_edges += int(infos[i]["edges"])
+    wl.close()
+    pl_gteps = sum_over_ranks(pl_edges, world, dev) / max_over_ranks(pl_wall, world, dev) / 1e9
+    pl_gteps_dev = sum_over_ranks(pl_edges, world, dev) / max_over_ranks(pl_dev, world, dev) / 1e9
+    per_launch = {"gteps_wall": round(pl_gteps, 4), "gteps_device": round(pl_gteps_dev, 4), "sample": len(pl_idx),
+                  "form": "each sampled query alone, one persistent launch, host waits for its status; "
+                          "R-MAT BFS direction-optimising, grid queries with 15 CTA-local sub-rounds"}
+    lat_ms = {"p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+              "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3), "max_ms": round(1e3 * float(lat.max()), 3)}
+    if embedded:
+        srv.close()
+        for d in dgs:
+            d.close()
+        ctx.close()
+        if rank != 0:
+            return None
+        return {
+            "workload": (f"serve: Poisson {args.rate:g} q/s for {args.duration:g} s, 70% BFS / 30% SSSP, R-MAT scale "
+                         f"{args.serve_scale} (ef 16) + 32 grids of side U[256,2048]"),
+            "queries": nq, "gteps": round(value, 4), **lat_ms, "served_in_s": round(span, 3),
+            "per_launch": per_launch, "served_vs_per_launch": round(value / pl_gteps, 3),
+            "clock": "host wall clock for both forms (served: first submission to last result in host memory)",
+            "verified_against_oracle": len(verify), "slots": args.slots, "epoch_rounds": args.epoch_rounds,
+            "tuning": {**ctx.default_tuning, **(tuning or {})}, "clocks": clk,
+        }
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": nq,
@@ -825,9 +1004,8 @@ def run_serve(args, world, rank, local):
                            queries=nq, slots=args.slots, epoch_rounds=args.epoch_rounds,
                            arena_entries=st["arena_entries"], tuning={**ctx.default_tuning, **(tuning or {})},
                            parallelism=f"replicas x{world} (independent arrival streams)"),
-            "latency": {"p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
-                        "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
-                        "max_ms": round(1e3 * float(lat.max()), 3)},
+            "latency": lat_ms,
+            "per_launch": per_launch, "served_vs_per_launch": round(value / pl_gteps, 3),
             "server": {k: st[k] - base.get(k, 0) if k in ("completed", "epochs", "rounds", "edges", "solo") else st[k]
                        for k in ("completed", "rejected", "epochs", "rounds", "edges", "busy_s", "kernel_s", "grid",
                                  "cta_size", "solo")},

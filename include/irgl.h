@@ -118,6 +118,17 @@ typedef struct {
                                     arrays (by default one 64-bit word per vertex holds both,
                                     lowered by one atomicMin, and the distances are copied to the
                                     output at the end) */
+#define IRGL_TUNE_NO_BCAST 0x10u /* persistent BFS, SSSP and CC: run small-frontier rounds like the
+                                    others. By default a round whose frontier has at most 768 items
+                                    (and at most 2^20 / grid) skips the degree bins and the grid-wide
+                                    list of long adjacency lists: every CTA reads the whole frontier,
+                                    scans its degrees in shared memory and relaxes an equal share of
+                                    its edges (one grid barrier per round instead of two) */
+#define IRGL_TUNE_THREAD_BIN 0x20u /* all kernels: the lane that popped an adjacency list of 1..4 edges
+                                    walks it itself (no per-edge search or shuffle) instead of the warp's
+                                    scan bin dealing it out with the other short lists. Off by default:
+                                    on R-MAT scale 20 the scan bin's denser strips win (SSSP 627 vs
+                                    643 us per query, 256-instance batch 14.1 vs 13.5 GTEPS) */
 
 /* Per-call counters. */
 typedef struct {
@@ -242,9 +253,13 @@ irgl_status irgl_run(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uint32_t
  * Per-round trace of persistent launches on this context (Iterate and batch):
  * after each round's grid barrier one thread records the globaltimer time
  * (ns), the round's in-worklist size and its out-worklist size. Record 0 is
- * the end of the prologue (state initialisation). irgl_trace_enable(ctx, 0)
- * switches tracing off; enabling allocates 16 bytes per round of capacity.
- * irgl_trace_read copies min(cap, rounds of the last launch + 1) records. */
+ * the end of the prologue (state initialisation); for single-query Iterates
+ * its out field holds the prologue's duration in ns (from the kernel's start).
+ * Record rounds + 1, when the capacity has room for it, is the end of the
+ * epilogue (results written), marked with in = out = 0xFFFFFFFF.
+ * irgl_trace_enable(ctx, 0) switches tracing off; enabling allocates 16 bytes
+ * per round of capacity. irgl_trace_read copies min(cap, capacity, rounds of
+ * the last launch + 2) records. */
 irgl_status irgl_trace_enable(irgl_ctx* ctx, uint32_t max_rounds);
 irgl_status irgl_trace_read(irgl_ctx* ctx, uint64_t* t_ns, uint32_t* in_n, uint32_t* out_n, uint32_t cap,
                             uint32_t* nrec);
@@ -260,9 +275,11 @@ irgl_status irgl_control_cta(const uint32_t* masks, uint32_t count, uint32_t pre
 
 /* ---------------------------------------------------------------- autotuning
  * Coordinate descent over the irgl_tuning fields (CTA size, CTA and warp
- * degree thresholds, chunk, CTAs per SM; for BFS and SSSP also the CTA-local
- * sub-rounds, flags = IRGL_TUNE_LOCAL(0, 4 or 15); for SSSP also the near-far
- * delta), each candidate timed as the median
+ * degree thresholds, chunk, CTAs per SM, total grid max_blocks in {full, 1, 2,
+ * 8, 32, SMs}; for BFS and SSSP also the CTA-local sub-rounds, flags =
+ * IRGL_TUNE_LOCAL(0, 4 or 15), and for BFS on a graph with in-edges (or a
+ * symmetric one) IRGL_TUNE_DIROPT; for SSSP also the near-far delta), each
+ * candidate timed as the median
  * CUDA-event time of `reps` persistent Iterate runs of kernel k from the given
  * sources on graph g (after one warm-up run). *best receives the fastest
  * tuning and *best_ms its time. Results do not depend on the tuning (the

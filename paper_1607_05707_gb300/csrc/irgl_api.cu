@@ -49,6 +49,8 @@ DeviceGuard::~DeviceGuard() {
   if (prev_ != dev_) cudaSetDevice(prev_);
 }
 
+uint32_t thread_bin(const irgl_tuning& t) { return (t.flags & IRGL_TUNE_THREAD_BIN) ? kThreadBin : 0u; }
+
 irgl_tuning default_tuning() {
   irgl_tuning t;
   t.cta_size = 128;
@@ -266,6 +268,7 @@ KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tu
   p.tn.warp_thresh = t.warp_thresh;
   p.tn.cta_thresh = t.cta_thresh;
   p.tn.chunk = t.chunk;
+  p.tn.thread_max = thread_bin(t);
   p.max_rounds = 0xFFFFFFFFu;
   p.timeout_ns = ctx->dbg_timeout_us ? ctx->dbg_timeout_us * 1000ull : 2000000000ull;
   p.skip_cta = -1;
@@ -274,6 +277,7 @@ KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tu
   p.trace_cap = ctx->trace_cap;
   p.big = (t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{ctx->big_e, ctx->big_off, ctx->big_cap};
   if (ctx->dbg_big_cap && p.big.cap > ctx->dbg_big_cap) p.big.cap = ctx->dbg_big_cap;
+  p.bcast = (t.flags & IRGL_TUNE_NO_BCAST) ? 0u : 1u;
   if ((t.flags & IRGL_TUNE_DIROPT) && (g->in_row_ptr || (g->flags & IRGL_SYMMETRIC))) {
     p.in_row_ptr = g->in_row_ptr ? g->in_row_ptr : g->row_ptr;
     p.in_col = g->in_row_ptr ? g->in_col : g->col;
@@ -401,7 +405,7 @@ irgl_status irgl_trace_read(irgl_ctx* ctx, uint64_t* t_ns, uint32_t* in_n, uint3
   *nrec = 0;
   if (!ctx->trace) return IRGL_OK;
   DeviceGuard guard(ctx->device);
-  const uint32_t k = std::min(std::min(cap, ctx->trace_cap), ctx->st_host->rounds + 1);
+  const uint32_t k = std::min(std::min(cap, ctx->trace_cap), ctx->st_host->rounds + 2);
   std::vector<unsigned long long> buf(2 * (size_t)k);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e == cudaSuccess && k)

@@ -52,6 +52,7 @@ struct irgl_batch {
   std::vector<BQuery> qs;
   bool prepared = false;
   uint64_t arena_n = 0;
+  uint64_t wl_cap = 0;  // entries of each worklist
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   DevStatus* st = nullptr;
@@ -81,6 +82,7 @@ struct irgl_batch {
   uint32_t big_cap = 0;
   irgl_tuning t{};
   uint32_t grid = 0;
+  uint32_t id_step = 1;  // round ids per round: 1 + CTA-local sub-rounds
   BParams bp{};
   uint32_t admit_grid = 0;
   bool graph_ok = false;
@@ -325,8 +327,14 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
     if (packed) e = cudaMalloc(&b->ds, sizeof(unsigned long long) * b->arena_n);
     else e = cudaMalloc(&b->stamp, sizeof(uint32_t) * b->arena_n);
   }
-  if (e == cudaSuccess) e = cudaMalloc(&b->items[0], sizeof(uint32_t) * b->arena_n);
-  if (e == cudaSuccess) e = cudaMalloc(&b->items[1], sizeof(uint32_t) * b->arena_n);
+  // worklists: one entry per arena vertex; with CTA-local sub-rounds a vertex
+  // lowered again in a later sub-round of the same round can be on the next
+  // round's worklist twice, so they get twice the room (a round that still
+  // overflows reports IRGL_ERR_WL_OVERFLOW)
+  const bool sub = packed && ((t.flags >> 8) & 15u) != 0;
+  b->wl_cap = std::min<uint64_t>(b->arena_n * (sub ? 2u : 1u), 0xFFFFFFF0ull);
+  if (e == cudaSuccess) e = cudaMalloc(&b->items[0], sizeof(uint32_t) * b->wl_cap);
+  if (e == cudaSuccess) e = cudaMalloc(&b->items[1], sizeof(uint32_t) * b->wl_cap);
   if (e == cudaSuccess) e = cudaMalloc(&b->qlast, sizeof(uint32_t) * Q);
   if (e == cudaSuccess) e = cudaMallocHost(&b->qlast_host, sizeof(uint32_t) * Q);
   if (e == cudaSuccess) e = cudaMalloc(&b->qfirst, sizeof(uint32_t) * Q);
@@ -386,10 +394,10 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   b->bp.qlast = b->qlast;
   b->bp.items[0] = b->items[0];
   b->bp.items[1] = b->items[1];
-  b->bp.cap = static_cast<uint32_t>(b->arena_n);
+  b->bp.cap = static_cast<uint32_t>(b->wl_cap);
   b->bp.cont = b->cont;
   b->bp.st = b->st;
-  b->bp.tn = Tune{t.warp_thresh, t.cta_thresh, t.chunk};
+  b->bp.tn = Tune{t.warp_thresh, t.cta_thresh, t.chunk, thread_bin(t)};
   b->bp.max_rounds = 0xFFFFFFFFu;
   b->bp.rounds_cap_is_error = 1;
   b->bp.timeout_ns = ctx->dbg_timeout_us ? ctx->dbg_timeout_us * 1000ull : 2000000000ull;
@@ -402,6 +410,8 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   b->bp.far_items[1] = b->far_items[1];
   b->bp.far_cap = nf ? static_cast<uint32_t>(b->arena_n) : 0u;
   b->bp.far_stamp = b->far_stamp;
+  b->bp.local_rounds = b->ds ? (t.flags >> 8) & 15u : 0u;
+  b->id_step = b->bp.local_rounds + 1u;
   b->aps.clear();
   for (const Wave& wv : b->waves) {
     AdmitParams ap{};
@@ -417,9 +427,10 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
     ap.delta = b->bp.delta;
     ap.items[0] = b->items[0];
     ap.items[1] = b->items[1];
-    ap.cap = static_cast<uint32_t>(b->arena_n);
+    ap.cap = static_cast<uint32_t>(b->wl_cap);
     ap.cont = b->cont;
     ap.st = b->st;
+    ap.id_step = b->id_step;
     b->aps.push_back(ap);
   }
   b->admit_grid = static_cast<uint32_t>(ctx->sm_count) * 4;
@@ -485,7 +496,7 @@ irgl_status irgl_batch_sync(irgl_batch* b, irgl_stats* stats) {
   b->ctx->st_host->rounds = st.rounds;  // lets irgl_trace_read size a batch trace (the last wave's)
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
-    stats->rounds = st.epoch - b->epoch_prev;  // every wave's rounds
+    stats->rounds = (st.epoch - b->epoch_prev) / b->id_step;  // every wave's rounds
     stats->grid = b->grid;
     stats->cta_size = b->t.cta_size;
     // per wave: fill, sources, iterate; then the result extraction
@@ -508,7 +519,9 @@ irgl_status irgl_batch_sync(irgl_batch* b, irgl_stats* stats) {
     return s;
   }
   // per-instance rounds from the termination flags and the round its wave began at
-  for (uint32_t i = 0; i < Q; ++i) b->qs[i].rounds = b->qlast_host[i] - b->qfirst_host[i] + 2;
+  for (uint32_t i = 0; i < Q; ++i)
+    b->qs[i].rounds = static_cast<uint32_t>(static_cast<int32_t>(b->qlast_host[i] - b->qfirst_host[i]) /
+                                            static_cast<int32_t>(b->id_step) + 2);
   b->epoch_prev = st.epoch;
   cudaMemsetAsync(&b->st->edges, 0, sizeof(unsigned long long), b->stream);
   if (st.epoch > 0xF0000000u) batch_reset_status(b);
@@ -538,7 +551,7 @@ irgl_status irgl_batch_autotune(irgl_batch* b, uint32_t reps, irgl_tuning* best,
   };
   bool has_sssp = false;  // near-far delta is searched when the batch holds SSSP queries
   for (const BQuery& q : b->qs) has_sssp |= q.op == IRGL_SSSP;
-  irgl_status s = tune_descend(measure, best, best_ms, has_sssp);
+  irgl_status s = tune_descend(measure, best, best_ms, has_sssp, true);
   if (s != IRGL_OK) return s;
   // then the wave budget: a quarter, half (the default) and all of the L2, and one wave
   int l2 = 0;

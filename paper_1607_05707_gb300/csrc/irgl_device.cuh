@@ -133,7 +133,9 @@ struct Tune {
   uint32_t warp_thresh;
   uint32_t cta_thresh;
   uint32_t chunk;
+  uint32_t thread_max;  // lists of 1..thread_max edges are walked by the lane that popped them (0 = none)
 };
+constexpr uint32_t kThreadBin = 4;
 
 // Single-graph kernel parameters.
 struct KParams {
@@ -178,6 +180,8 @@ struct KParams {
   // its tiles a CTA expands what it pushed to its shared-memory stage, up to
   // this many more times, before flushing the rest to the out-worklist
   uint32_t local_rounds;
+  // rounds over small frontiers run without the big list (broadcast_round); 0 = off
+  uint32_t bcast;
 };
 
 // Per-launch (one round) arguments.
@@ -234,6 +238,10 @@ struct BParams {
   uint32_t* far_items[2];   // far lists of arena indices
   uint32_t far_cap;
   uint32_t* far_stamp;      // arena: round id of the far list a vertex was last put on
+  // CTA-local sub-rounds per round (0 = off). Round r then owns the ids
+  // ep0 + r (k + 1) .. ep0 + r (k + 1) + k: its base id marks pushes (qlast)
+  // and the far lists, sub-round j stamps packed words with base + j
+  uint32_t local_rounds;
 };
 
 // ----------------------------------------------------------------------------- small helpers
@@ -721,7 +729,11 @@ __device__ __forceinline__ void decide_n(const RoundCtx& rc, uint32_t* state, ui
   for (int k = 0; k < N; ++k) {
     const uint32_t o = OP == OP_RUNTIME ? op[k] : OP;
     nd[k] = o == OP_SSSP ? val[k] + static_cast<uint32_t>(wt[k]) : (o == OP_BFSR ? val[k] + 1u : val[k]);
-    t[k] = ((valid >> k) & 1u) != 0 && (o == OP_BFS ? cur[k] == kInf : nd[k] < cur[k]);
+    // BFS takes unvisited vertices only, except batched BFS under CTA-local
+    // sub-rounds, where a vertex can be reached before its level is final
+    // and later lowered (unit-weight relaxation: same fixed point)
+    const bool first_only = o == OP_BFS && !(OP == OP_RUNTIME && rc.local_rounds != 0);
+    t[k] = ((valid >> k) & 1u) != 0 && (first_only ? cur[k] == kInf : nd[k] < cur[k]);
   }
   // near-far: an improvement to a value >= the limit goes to the far list,
   // deduplicated per phase by far_stamp (route 2)
@@ -968,8 +980,10 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
         // a CTA-local pop: take the value and clear the round stamp in one
         // atomic, so an improvement that lands after this read (from any CTA,
         // in any sub-round) pushes the vertex again instead of counting on a
-        // pending expansion that has just happened
-        val = static_cast<uint32_t>(atomicAnd(rc.ds + item, 0xFFFFFFFF00000000ull) >> 32);
+        // pending expansion that has just happened (a batched BFS item carries
+        // the level its out-edges assign, its own + 1)
+        val = static_cast<uint32_t>(atomicAnd(rc.ds + item, 0xFFFFFFFF00000000ull) >> 32) +
+              (OP == OP_RUNTIME && op == OP_BFS ? 1u : 0u);
       else if (kPackedOp<OP> && rc.ds != nullptr && (OP != OP_RUNTIME || op != OP_BFS))
         val = static_cast<uint32_t>(__ldcg(rc.ds + item) >> 32);
       else if (op == OP_BFS)
@@ -1060,11 +1074,57 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
     pushed |= p;
   }
 
+  // Thread bin (opt-in): a list of at most thread_max (<= 4) edges is walked by
+  // the lane that popped it, all its loads and atomics in flight together; no
+  // search or shuffle per edge (meshes and grids have nothing else).
+  const bool tiny = valid && deg > 0 && deg <= rc.tn.thread_max && deg < rc.tn.warp_thresh && deg < split;
+  if (__any_sync(kFull, tiny)) {
+    uint32_t v[kThreadBin], cur[kThreadBin], sbv[kThreadBin], opv[kThreadBin], ovv[kThreadBin], rr[kThreadBin],
+        ndv[kThreadBin];
+    int32_t wt[kThreadBin];
+    uint32_t vmask = 0;
+    const uint32_t oq = tiny ? g.op(q) : static_cast<uint32_t>(OP_BFS);
+    const uint32_t sq = tiny ? g.sbase(q) : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < kThreadBin; ++k) {
+      v[k] = 0;
+      wt[k] = 0;
+      sbv[k] = sq;
+      opv[k] = oq;
+      ovv[k] = val;
+      if (tiny && k < deg) {
+        v[k] = ld_adj(g.colp(q) + beg + k);
+        if (needs_w<OP>(oq)) wt[k] = ld_adj(g.wp(q) + beg + k);
+        vmask |= 1u << k;
+      }
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < kThreadBin; ++k)
+      cur[k] = ((vmask >> k) & 1u) ? load_cur<OP>(rc, g.state + sq, sq, v[k]) : 0u;
+    decide_n<OP, kThreadBin>(rc, g.state, g.stamp, opv, sbv, v, ovv, wt, cur, vmask, rr, ndv);
+    uint32_t f = 0, ff = 0, dmin = kInf;
+#pragma unroll
+    for (uint32_t k = 0; k < kThreadBin; ++k) {
+      if (rr[k] == 1u) f |= 1u << k;
+      if (rr[k] == 2u) {
+        ff |= 1u << k;
+        dmin = min(dmin, ndv[k]);
+      }
+    }
+    if ((f | ff) != 0u) {
+      if (RED == RED_ALL) sm.pushed[tid] = 1;
+      if (V::kBatched) g.mark(q, rc.ep);
+    }
+    push4<CTA>(sm, rc.out, f, sq + v[0], sq + v[1], sq + v[2], sq + v[3]);
+    if (kNearFarOp<OP>) push_far4<CTA>(sm, rc.far_out, ff, sq + v[0], sq + v[1], sq + v[2], sq + v[3], dmin);
+    pushed |= (f | ff) != 0;
+  }
+
   // Scan bin, per warp: the short lists of the warp's 32 items are dealt out
   // four edges per lane per strip (strided by 32, so loads coalesce within a
   // list); each edge finds its list by a shuffle binary search over the
   // warp's exclusive degree prefix. No CTA barrier is involved.
-  const bool small = valid && deg > 0 && deg < rc.tn.warp_thresh && deg < split;
+  const bool small = valid && deg > 0 && deg < rc.tn.warp_thresh && deg < split && !tiny;
   const uint32_t sdeg = small ? deg : 0u;
   const uint32_t sincl = warp_incl_scan(sdeg);
   const uint32_t sexcl = sincl - sdeg;
@@ -1167,7 +1227,7 @@ __device__ __forceinline__ void round_body(const V& g, Smem<CTA>& sm, const Roun
   // pushes the vertex again; the relaxation is label-correcting, so the fixed
   // point is the same. What is left unexpanded is flushed to the out-worklist.
   uint32_t lo = 0;
-  if (kPackedOp<OP> && !V::kBatched && rc.local_rounds != 0) {
+  if (kPackedOp<OP> && rc.ds != nullptr && rc.local_rounds != 0) {
     RoundCtx lc = rc;
     for (uint32_t j = 1; j <= rc.local_rounds; ++j) {
       __syncthreads();
@@ -1183,6 +1243,136 @@ __device__ __forceinline__ void round_body(const V& g, Smem<CTA>& sm, const Roun
   }
   __syncthreads();
   flush_stage<CTA>(sm, rc.out, lo);
+}
+
+// ----------------------------------------------------------------------------- small-frontier round
+
+// Frontier size up to which a single-query round may run without the big
+// list: every CTA reads the whole frontier, so the limit also bounds the
+// frontier x grid product (broadcast reads of at most about 1 M items).
+constexpr uint32_t kBcast = 768;
+constexpr unsigned long long kBcastBudget = 1ull << 20;
+
+// Exclusive prefix sum of a[0, n) in place (n <= kBcast), every thread of the
+// CTA calling; returns the total. wt: shared scratch of CTA / 32 + 1 words.
+template <int CTA>
+__device__ __forceinline__ uint32_t cta_excl_scan(uint32_t* a, uint32_t n, uint32_t* wt) {
+  constexpr uint32_t PER = (kBcast + CTA - 1) / CTA;
+  constexpr uint32_t W = CTA / 32;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t i0 = threadIdx.x * PER;
+  uint32_t loc[PER];
+  uint32_t sum = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < PER; ++k) {
+    loc[k] = i0 + k < n ? a[i0 + k] : 0u;
+    sum += loc[k];
+  }
+  const uint32_t incl = warp_incl_scan(sum);
+  if (lane == 31) wt[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t x = lane < W ? wt[lane] : 0u;
+    const uint32_t xi = warp_incl_scan(x);
+    if (lane < W) wt[lane] = xi - x;
+    if (lane == 31) wt[W] = xi;
+  }
+  __syncthreads();
+  uint32_t run = wt[warp] + incl - sum;
+#pragma unroll
+  for (uint32_t k = 0; k < PER; ++k) {
+    if (i0 + k < n) a[i0 + k] = run;
+    run += loc[k];
+  }
+  const uint32_t total = wt[W];
+  __syncthreads();
+  return total;
+}
+
+// One round of a single-query Iterate over a small frontier (in_n <= kBcast):
+// instead of binning the popped vertices by degree and sending long lists
+// through the grid-wide big list (an append, a second grid barrier and a
+// search), every CTA reads all in_n items and their row offsets, scans the
+// degrees in shared memory and walks an equal share of the concatenated
+// edges, four per thread per strip, each edge's list found by a binary search
+// of the shared offsets. Same pops, operator and pushes as round_body; the
+// round's dependent chain is shorter by the big-list append, the barrier
+// between the phases and the search in global memory.
+template <uint32_t OP, int CTA>
+__device__ __forceinline__ void broadcast_round(const SingleView<OP>& g, Smem<CTA>& sm, const RoundCtx& rc,
+                                                uint32_t& edges) {
+  __shared__ uint32_t b_beg[kBcast];
+  __shared__ uint32_t b_off[kBcast];
+  __shared__ uint32_t b_val[kBcast];
+  __shared__ uint32_t b_wt[CTA / 32 + 1];
+  const uint32_t n_in = rc.in_n;
+  for (uint32_t i = threadIdx.x; i < n_in; i += CTA) {
+    const uint32_t u = rc.in_items ? __ldcg(rc.in_items + i) : i;
+    uint32_t b = 0, e = 0, val = 0;
+    if (u < g.n) {
+      b = __ldg(g.row_ptr + u);
+      e = __ldg(g.row_ptr + u + 1);
+      if (OP == OP_BFS) val = rc.bfs_val;
+      else if (kPackedOp<OP> && rc.ds != nullptr) val = static_cast<uint32_t>(__ldcg(rc.ds + u) >> 32);
+      else val = __ldcg(g.state + u);
+    } else {
+      set_err(rc.out.err, DERR_BAD_ITEM);
+    }
+    b_beg[i] = b;
+    b_off[i] = e - b;
+    b_val[i] = val;
+  }
+  __syncthreads();
+  const uint32_t total = cta_excl_scan<CTA>(b_off, n_in, b_wt);
+  const uint32_t lo = static_cast<uint32_t>(static_cast<unsigned long long>(total) * blockIdx.x / gridDim.x);
+  const uint32_t hi = static_cast<uint32_t>(static_cast<unsigned long long>(total) * (blockIdx.x + 1) / gridDim.x);
+  if (threadIdx.x == 0) edges += hi - lo;  // per-thread counters are summed over the CTA
+  constexpr uint32_t E = 4;
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t base = lo; base < hi; base += E * CTA) {
+    uint32_t v[E], cur[E], sb[E], op[E], ov[E], rr[E], ndv[E];
+    int32_t wt[E];
+    uint32_t vmask = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < E; ++k) {
+      const uint32_t e = base + k * CTA + tid;
+      v[k] = 0;
+      wt[k] = 0;
+      sb[k] = 0;
+      op[k] = OP;
+      ov[k] = 0;
+      if (e < hi) {
+        // last list whose first edge is <= e (lists of degree 0 share offsets: the search skips them)
+        uint32_t a = 0, z = n_in - 1;
+        while (a < z) {
+          const uint32_t md = (a + z + 1) >> 1;
+          if (b_off[md] <= e) a = md;
+          else z = md - 1;
+        }
+        const uint32_t edge = b_beg[a] + (e - b_off[a]);
+        ov[k] = b_val[a];
+        v[k] = ld_adj(g.col + edge);
+        if (needs_w<OP>(OP)) wt[k] = ld_adj(g.w + edge);
+        vmask |= 1u << k;
+      }
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < E; ++k) cur[k] = ((vmask >> k) & 1u) ? load_cur<OP>(rc, g.state, 0u, v[k]) : 0u;
+    decide_n<OP, 4>(rc, g.state, g.stamp, op, sb, v, ov, wt, cur, vmask, rr, ndv);
+    uint32_t f = 0, ff = 0, dmin = kInf;
+#pragma unroll
+    for (uint32_t k = 0; k < E; ++k) {
+      f |= (rr[k] == 1u ? 1u : 0u) << k;
+      if (kNearFarOp<OP> && rr[k] == 2u) {
+        ff |= 1u << k;
+        dmin = min(dmin, ndv[k]);
+      }
+    }
+    push4<CTA>(sm, rc.out, f, v[0], v[1], v[2], v[3]);
+    if (kNearFarOp<OP>) push_far4<CTA>(sm, rc.far_out, ff, v[0], v[1], v[2], v[3], dmin);
+  }
+  __syncthreads();
+  flush_stage<CTA>(sm, rc.out);
 }
 
 // ----------------------------------------------------------------------------- grid barrier
@@ -1430,29 +1620,102 @@ __device__ __forceinline__ void init_smem(Smem<CTA>& sm) {
 // in-edges for a parent at the current level L and, at the first one, takes
 // level L + 1 (v is written by this thread only) and joins the out-worklist.
 // Same levels as the top-down round (the fixed point is unique); the work is
-// the in-edges scanned until a parent is found.
+// the in-edges scanned until a parent is found. Only a parent at exactly L
+// counts: an unvisited vertex has no visited in-neighbour below L, and one
+// found in this round (L + 1) is not a parent yet. Each thread takes four
+// vertices at once (strided by the CTA size, so every load coalesces) and
+// checks two in-edges of each per step for up to four steps, so eight
+// independent chains of loads are in flight per thread; what is still open
+// after that (in-lists longer than eight) is scanned by the whole warp, 64
+// in-edges per step, so one long list does not hold the warp for hundreds
+// of dependent steps.
 template <int CTA>
 __device__ __forceinline__ void bottom_up_round(const KParams& p, Smem<CTA>& sm, const RoundCtx& rc, uint32_t L,
                                                 uint32_t& edges) {
-  for (uint32_t base = blockIdx.x * CTA; base < p.n; base += gridDim.x * CTA) {
-    const uint32_t v = base + threadIdx.x;
-    bool found = false;
-    if (v < p.n && __ldcg(p.state + v) == kInf) {
-      const uint32_t b = __ldg(p.in_row_ptr + v), e = __ldg(p.in_row_ptr + v + 1);
-      for (uint32_t k = b; k < e; ++k) {
-        ++edges;
-        if (__ldcg(p.state + ld_adj(p.in_col + k)) == L) {
-          found = true;
-          break;
+  constexpr uint32_t J = 4;
+  constexpr uint32_t kLaneSteps = 4;
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint32_t base = blockIdx.x * (CTA * J); base < p.n; base += gridDim.x * (CTA * J)) {
+    uint32_t v[J], b[J], e[J], ob[J], oe[J];
+    bool open[J], found[J];
+#pragma unroll
+    for (uint32_t j = 0; j < J; ++j) {
+      v[j] = base + j * CTA + threadIdx.x;
+      open[j] = v[j] < p.n && __ldcg(p.state + v[j]) == kInf;
+      found[j] = false;
+    }
+#pragma unroll
+    for (uint32_t j = 0; j < J; ++j) {
+      b[j] = open[j] ? __ldg(p.in_row_ptr + v[j]) : 0u;
+      e[j] = open[j] ? __ldg(p.in_row_ptr + v[j] + 1) : 0u;
+      // out-degree of v for the direction rule, loaded with the in-offsets (coalesced)
+      ob[j] = open[j] ? __ldg(p.row_ptr + v[j]) : 0u;
+      oe[j] = open[j] ? __ldg(p.row_ptr + v[j] + 1) : 0u;
+      open[j] = open[j] && b[j] < e[j];
+    }
+    for (uint32_t step = 0; step < kLaneSteps; ++step) {
+      uint32_t c[J][2];
+#pragma unroll
+      for (uint32_t j = 0; j < J; ++j) {
+#pragma unroll
+        for (uint32_t t = 0; t < 2; ++t) c[j][t] = (open[j] && b[j] + t < e[j]) ? ld_adj(p.in_col + b[j] + t) : kInf;
+      }
+      bool any = false;
+#pragma unroll
+      for (uint32_t j = 0; j < J; ++j) {
+        bool hit = false;
+#pragma unroll
+        for (uint32_t t = 0; t < 2; ++t) hit |= c[j][t] != kInf && __ldcg(p.state + c[j][t]) == L;
+        if (open[j]) {
+          const uint32_t left = e[j] - b[j];
+          edges += left < 2u ? left : 2u;
+          b[j] += 2u;
+          found[j] = hit;
+          open[j] = !hit && b[j] < e[j];
+        }
+        any |= open[j];
+      }
+      if (!__any_sync(kFull, any)) break;
+    }
+    // long in-lists: the warp takes the open vertices one at a time
+#pragma unroll
+    for (uint32_t j = 0; j < J; ++j) {
+      for (;;) {
+        const unsigned m = __ballot_sync(kFull, open[j]);
+        if (m == 0) break;
+        const int ld = __ffs(m) - 1;
+        uint32_t kb = __shfl_sync(kFull, b[j], ld);
+        const uint32_t ke = __shfl_sync(kFull, e[j], ld);
+        bool hit = false;
+        while (kb < ke) {
+          const uint32_t k0 = kb + lane, k1 = kb + 32u + lane;
+          const uint32_t c0 = k0 < ke ? ld_adj(p.in_col + k0) : kInf;
+          const uint32_t c1 = k1 < ke ? ld_adj(p.in_col + k1) : kInf;
+          const bool h = (c0 != kInf && __ldcg(p.state + c0) == L) || (c1 != kInf && __ldcg(p.state + c1) == L);
+          const uint32_t span = ke - kb < 64u ? ke - kb : 64u;
+          if (lane == 0) edges += span;
+          kb += 64u;
+          if (__any_sync(kFull, h)) {
+            hit = true;
+            break;
+          }
+        }
+        if (lane == static_cast<uint32_t>(ld)) {
+          open[j] = false;
+          found[j] = hit;
         }
       }
-      if (found) {
-        __stcg(p.state + v, L + 1u);
-        if (p.vis) atomicOr(p.vis + (v >> 5), 1u << (v & 31u));
-        atomicAdd(&sm.mf_cta, static_cast<unsigned long long>(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
+    }
+#pragma unroll
+    for (uint32_t j = 0; j < J; ++j) {
+      if (found[j]) {
+        __stcg(p.state + v[j], L + 1u);
+        if (p.vis) atomicOr(p.vis + (v[j] >> 5), 1u << (v[j] & 31u));
+        atomicAdd(&sm.mf_cta, static_cast<unsigned long long>(oe[j] - ob[j]));
       }
     }
-    push1<CTA>(sm, rc.out, found, v);
+#pragma unroll
+    for (uint32_t j = 0; j < J; ++j) push1<CTA>(sm, rc.out, found[j], v[j]);
     if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
   }
   __syncthreads();
@@ -1540,7 +1803,7 @@ template <int CTA>
 __device__ __forceinline__ void persistent_exit(Smem<CTA>& sm, DevStatus* st, bool ok, uint32_t rounds,
                                                 uint32_t last_out, uint32_t ep0, unsigned long long esum,
                                                 uint32_t* cont, uint32_t cont_buf, uint32_t far_buf = 0,
-                                                uint32_t far_n = 0) {
+                                                uint32_t far_n = 0, uint32_t id_step = 1) {
   __syncthreads();
   if (threadIdx.x == 0) {
     atomicAdd(&st->edges, esum);
@@ -1567,7 +1830,7 @@ __device__ __forceinline__ void persistent_exit(Smem<CTA>& sm, DevStatus* st, bo
     }
     st->rounds = rounds;
     st->last_out = last_out;
-    st->epoch = ep0 + rounds;  // round ids ep0 .. ep0 + rounds - 1 were used
+    st->epoch = ep0 + rounds * id_step;  // round ids ep0 .. ep0 + rounds * id_step - 1 were used
     for (int i = 0; i < 4; ++i) {
       st->tail[i] = 0;
       st->grab[i] = 0;
@@ -1591,9 +1854,31 @@ __device__ __forceinline__ void trace_round(unsigned long long* trace, uint32_t 
   }
 }
 
+// Record 0 of a trace: the end of the prologue, with the prologue's duration
+// (ns since the kernel started, t0 taken by CTA 0) in the out field.
+__device__ __forceinline__ void trace_prologue(unsigned long long* trace, uint32_t cap, unsigned long long t0,
+                                               uint32_t in_n) {
+  if (trace && cap > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long t = globaltimer_ns();
+    const unsigned long long d = t - t0;
+    trace[0] = t;
+    trace[1] = (static_cast<unsigned long long>(in_n) << 32) | static_cast<uint32_t>(d < 0xFFFFFFFFull ? d : 0xFFFFFFFFull);
+  }
+}
+
+// Record rounds + 1 of a trace: the end of the epilogue (results copied out),
+// marked with in = out = 0xFFFFFFFF.
+__device__ __forceinline__ void trace_end(unsigned long long* trace, uint32_t cap, uint32_t rounds) {
+  if (trace && rounds + 1 < cap && blockIdx.x == 0 && threadIdx.x == 0) {
+    trace[2 * (rounds + 1)] = globaltimer_ns();
+    trace[2 * (rounds + 1) + 1] = ~0ull;
+  }
+}
+
 // Iteration-outlined Iterate: every round in one cooperative launch.
 template <uint32_t OP, int CTA>
 __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& sm) {
+  const unsigned long long t_start = p.trace ? globaltimer_ns() : 0ull;
   init_smem<CTA>(sm);
   DevStatus* st = p.st;
   uint32_t gen = 0;
@@ -1635,7 +1920,7 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < (p.n + 31u) >> 5; i += gridDim.x * CTA) __stcg(p.vis + i, 0u);
   }
   if (ok) ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
-  trace_round(p.trace, p.trace_cap, 0, init_n, 0);
+  trace_prologue(p.trace, p.trace_cap, t_start, init_n);
 
   // Near-far schedule (SSSP distances, CC labels): improvements to a value >=
   // limit wait on a far list; when a round pushes nothing below the limit, a
@@ -1655,6 +1940,9 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   unsigned long long visited_edges = 0;
   uint32_t prev_n = init_n;
   uint32_t in_n = init_n;
+  // small frontiers skip the big list (broadcast_round): BFS, SSSP and
+  // min-label CC rounds (near-far included) without CTA-local sub-rounds
+  const bool bcast = p.bcast != 0 && (OP == OP_BFS || OP == OP_SSSP || OP == OP_CC) && p.local_rounds == 0;
   for (uint32_t r = 0; ok; ++r) {
     uint32_t* const cur = (r & 1) ? p.items[1] : p.items[0];  // no dynamic index into the param struct
     uint32_t* const nxt = (r & 1) ? p.items[0] : p.items[1];
@@ -1699,6 +1987,8 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     } else if (dopt && bottom_up) {
       __syncthreads();
       bottom_up_round<CTA>(p, sm, rc, r, edges);
+    } else if (bcast && in_n <= kBcast && static_cast<unsigned long long>(in_n) * gridDim.x <= kBcastBudget) {
+      broadcast_round<OP, CTA>(g, sm, rc, edges);
     } else {
       round_body<OP, CTA, RED_NONE>(g, sm, rc, edges, dummy_t, dummy_f);
     }
@@ -1776,6 +2066,7 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
       __stcg(p.state + v, static_cast<uint32_t>(__ldcg(p.ds + v) >> 32));
   }
   const unsigned long long esum = cta_sum_u64<CTA>(sm, edges);
+  trace_end(p.trace, p.trace_cap, rounds);
   persistent_exit<CTA>(sm, st, ok, rounds, last_out, ep0, esum, nullptr, 0);
 }
 
@@ -1862,6 +2153,7 @@ __device__ __forceinline__ void cc_jump_persistent(const KParams& p, Smem<CTA>& 
     }
   }
   const unsigned long long esum = cta_sum_u64<CTA>(sm, edges);
+  trace_end(p.trace, p.trace_cap, rounds);
   persistent_exit<CTA>(sm, st, ok, rounds, 0, ep0, esum, nullptr, 0);
 }
 
@@ -1980,6 +2272,7 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
   bool ok = true;
   trace_round(p.trace, p.trace_cap, 0, init_n, 0);
   uint32_t in_n = init_n;
+  const uint32_t id_step = p.ds != nullptr ? p.local_rounds + 1u : 1u;
   for (uint32_t r = 0; ok; ++r) {
     RoundCtx rc;
     rc.in_n = in_n;
@@ -1987,7 +2280,7 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
     rc.in_items = b ? p.items[1] : p.items[0];
     rc.out = Out{b ? p.items[0] : p.items[1], &st->tail[(r + 1) % 3], p.cap, &st->err};
     rc.bfs_val = 0;
-    rc.ep = ep0 + r;
+    rc.ep = ep0 + r * id_step;
     rc.grab = &st->grab[r % 3];
     rc.tn = p.tn;
     rc.big = p.big;
@@ -2002,7 +2295,7 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
     rc.vis = nullptr;
     rc.ds = p.ds;     // round ids are the global ones: admission writes id 0
     rc.dsr = rc.ep;
-    rc.local_rounds = 0;
+    rc.local_rounds = p.ds != nullptr ? p.local_rounds : 0u;
     rc.local_items = nullptr;
     rc.far_in = nullptr;
     rc.far_in_n = 0;
@@ -2059,8 +2352,9 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
   if (nf && blockIdx.x == 0)  // every CTA holds the same limits
     for (uint32_t i = threadIdx.x; i < nq; i += CTA) p.blim[__ldg(&p.desc[i].slot)] = bs.lim[i];
   const unsigned long long esum = cta_sum_u64<CTA>(sm, edges);
+  trace_end(p.trace, p.trace_cap, rounds);
   persistent_exit<CTA>(sm, st, ok, rounds, last_out, ep0, esum, p.cont, (cur0 + rounds) & 1u,
-                       (fcur0 + rounds) & 1u, far_n);
+                       (fcur0 + rounds) & 1u, far_n, id_step);
 }
 
 // Admission of new queries into a batch: per new query j, arena range
@@ -2093,6 +2387,7 @@ struct AdmitParams {
   uint32_t* cont;
   DevStatus* st;
   uint32_t delta;
+  uint32_t id_step;       // round ids per round (1 + CTA-local sub-rounds)
 };
 
 __device__ __forceinline__ uint32_t find_new(const QNew* qn, uint32_t nnew, uint32_t i) {
@@ -2150,7 +2445,7 @@ __device__ __forceinline__ void admit_sources(const AdmitParams& a) {
   uint32_t* buf = (__ldcg(a.cont) & 1u) ? a.items[1] : a.items[0];
   const uint32_t ep = __ldcg(&a.st->epoch);
   for (uint32_t j = tid; j < a.nnew; j += nthreads) {
-    a.qlast[a.qn[j].slot] = ep - 1u;
+    a.qlast[a.qn[j].slot] = ep - a.id_step;  // "last pushed" one round before admission
     if (a.qfirst != nullptr) a.qfirst[a.qn[j].slot] = ep;
     if (a.blim != nullptr) a.blim[a.qn[j].slot] = a.delta;
   }

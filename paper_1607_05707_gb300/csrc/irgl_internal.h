@@ -87,6 +87,7 @@ extern thread_local std::string g_last_error;
 irgl_status fail(irgl_status s, const char* fmt, ...);
 irgl_status cuda_fail(cudaError_t e, const char* what);
 irgl_tuning default_tuning();
+uint32_t thread_bin(const irgl_tuning& t);  // Tune::thread_max of a tuning
 irgl_status resolve_tuning(const irgl_tuning* in, irgl_tuning* out);
 irgl_status read_status(irgl_ctx* ctx, DevStatus* out);
 irgl_status status_from_device(const DevStatus& s);
@@ -102,7 +103,8 @@ irgl_status check_kernel_graph(irgl_kernel k, const irgl_graph* g);
 uint32_t op_of(irgl_kernel k);
 KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tuning& t);
 irgl_status tune_descend(const std::function<float(const irgl_tuning&)>& measure, irgl_tuning* best, float* best_ms,
-                         bool with_delta = false, bool with_local = false);
+                         bool with_delta = false, bool with_local = false, bool with_diropt = false,
+                         uint32_t sms = 0);
 
 }  // namespace irgl
 

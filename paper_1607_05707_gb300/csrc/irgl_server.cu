@@ -262,6 +262,8 @@ struct irgl_server {
   uint64_t scratch_n = 0;
   uint64_t arena_n = 0;
   uint32_t grid = 0;
+  uint32_t sub_rounds = 0;  // CTA-local sub-rounds of the batched kernel (packed arena only)
+  uint32_t id_step = 1;     // round ids per round: 1 + sub_rounds
   irgl_tuning t{};
   Arena arena;
   std::vector<uint32_t> free_slots;
@@ -394,8 +396,14 @@ void solo_step(irgl_server* s, const Request& rq) {
   if (r == IRGL_OK) {
     cudaEventRecord(s->ev[0], s->stream);
     const uint32_t src = rq.src;
+    // alone, a query takes the single-query defaults plus the server's
+    // direction-optimising BFS and round-form flags (the batched kernel's CTA
+    // size and sub-rounds are choices for many small queries, not for this one)
+    irgl_tuning solo_t = default_tuning();
+    solo_t.flags = s->t.flags & (IRGL_TUNE_NO_BCAST | IRGL_TUNE_THREAD_BIN |
+                                 (rq.op == IRGL_BFS ? IRGL_TUNE_DIROPT : 0u));
     r = irgl_run(s->solo_ctx, static_cast<irgl_kernel>(rq.op), rq.g, &src, 1, s->solo_state[k], 0, IRGL_PERSISTENT,
-                 nullptr, 0, &st);
+                 &solo_t, 0, &st);
     cudaEventRecord(s->ev[1], s->stream);
   }
   if (r == IRGL_OK) {
@@ -554,6 +562,7 @@ bool server_step(irgl_server* s) {
     ap.st = s->st;
     ap.blim = s->blim;
     ap.delta = s->blim ? s->t.delta : 0u;
+    ap.id_step = s->id_step;
     e = cudaMemcpyAsync(s->qnew, hq, sizeof(QNew) * fresh.size(), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->srcs, hs, sizeof(uint32_t) * nsrc, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = launch_admit(ap, static_cast<uint32_t>(s->ctx->sm_count) * 4, s->stream);
@@ -587,7 +596,7 @@ bool server_step(irgl_server* s) {
     bp.cap = static_cast<uint32_t>(s->arena_n);
     bp.cont = s->cont;
     bp.st = s->st;
-    bp.tn = Tune{s->t.warp_thresh, s->t.cta_thresh, s->t.chunk};
+    bp.tn = Tune{s->t.warp_thresh, s->t.cta_thresh, s->t.chunk, thread_bin(s->t)};
     bp.max_rounds = s->cfg.epoch_rounds;
     bp.rounds_cap_is_error = 0;
     bp.timeout_ns = 2000000000ull;
@@ -598,6 +607,7 @@ bool server_step(irgl_server* s) {
     bp.far_items[1] = s->far_items[1];
     bp.far_cap = s->blim ? static_cast<uint32_t>(s->arena_n) : 0u;
     bp.far_stamp = s->far_stamp;
+    bp.local_rounds = s->sub_rounds;
     if (e == cudaSuccess) e = cudaEventRecord(s->ep_ev[2 * p], s->stream);
     if (e == cudaSuccess) e = launch_batch_iterate(s->t.cta_size, s->grid, bp, s->stream);
     if (e == cudaSuccess) e = cudaEventRecord(s->ep_ev[2 * p + 1], s->stream);
@@ -635,7 +645,7 @@ bool server_step(irgl_server* s) {
       std::lock_guard<std::mutex> lk(s->mu);
       s->kernel_s += kms * 1e-3;
     }
-    const uint32_t last_ep = sh.epoch - 1;  // round id of the epoch's last round
+    const uint32_t last_ep = sh.epoch - s->id_step;  // round id of the epoch's last round
     const uint32_t* hl = s->h_qlast + static_cast<size_t>(q) * S;
     const uint32_t* hf = s->h_qfirst + static_cast<size_t>(q) * S;
     // finished queries: no push in the epoch's last round. Only queries still
@@ -683,7 +693,8 @@ bool server_step(irgl_server* s) {
         const Active& a = fin[k];
         hfd[k] = FinDesc{a.rq.g->row_ptr, a.base, a.n, static_cast<uint32_t>(total), a.slot};
         total += a.n;
-        pd.rounds.push_back(hl[a.slot] - hf[a.slot] + 2);
+        pd.rounds.push_back(static_cast<uint32_t>(static_cast<int32_t>(hl[a.slot] - hf[a.slot]) /
+                                                  static_cast<int32_t>(s->id_step) + 2));
       }
       e = cudaMemcpyAsync(s->fin, hfd, sizeof(FinDesc) * fin.size(), cudaMemcpyHostToDevice, s->stream);
       if (e == cudaSuccess && s->cfg.count_edges)
@@ -782,6 +793,8 @@ irgl_status irgl_server_create(irgl_ctx* ctx, const irgl_server_config* cfg, irg
   const bool packed = !(t.flags & IRGL_TUNE_NO_PACKED);
   // near-far for SSSP queries (packed words only): two far lists and a far stamp per vertex
   const bool nf = packed && t.delta != 0;
+  s->sub_rounds = packed ? (t.flags >> 8) & 15u : 0u;
+  s->id_step = s->sub_rounds + 1u;
   s->arena_n = std::min<uint64_t>(bytes / (nf ? 32 : (packed ? 20 : 16)), 0xFFFFFFF0ull);
   const uint32_t S = cfg->max_slots;
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);

@@ -21,7 +21,7 @@ struct Axis {
   std::vector<uint32_t> values;
 };
 
-std::vector<Axis> axes(bool with_delta, bool with_local) {
+std::vector<Axis> axes(bool with_delta, bool with_local, bool with_diropt, uint32_t sms) {
   std::vector<Axis> a = {
       {&irgl_tuning::cta_size, {128, 256, 512, 1024}},
       {&irgl_tuning::cta_thresh, {32, 64, 128, 256, 512, 1024, 4096}},
@@ -29,9 +29,20 @@ std::vector<Axis> axes(bool with_delta, bool with_local) {
       {&irgl_tuning::chunk, {1, 2, 4}},
       {&irgl_tuning::blocks_per_sm, {0, 1, 2, 4}},
   };
+  // total grid below one CTA per SM (blocks_per_sm cannot go there): a small
+  // graph's rounds then synchronise a few CTAs, or one CTA with no grid barrier
+  // at all (the barrier's occupancy bound of Sec. 3.4 is an upper bound only)
+  if (sms) a.push_back({&irgl_tuning::max_blocks, {0, 1, 2, 8, 32, sms}});
   if (with_delta) a.push_back({&irgl_tuning::delta, {0, 16, 32, 64, 128, 256, 512, 1024}});
-  // CTA-local sub-rounds; the only flag the search sets (the defaults have none)
-  if (with_local) a.push_back({&irgl_tuning::flags, {0, IRGL_TUNE_LOCAL(4), IRGL_TUNE_LOCAL(15)}});
+  // the flags the search sets (the defaults have none): CTA-local sub-rounds
+  // and, when the graph has in-edges, direction-optimising BFS
+  std::vector<uint32_t> fl = {0};
+  if (with_local) {
+    fl.push_back(IRGL_TUNE_LOCAL(4));
+    fl.push_back(IRGL_TUNE_LOCAL(15));
+  }
+  if (with_diropt) fl.push_back(IRGL_TUNE_DIROPT);
+  if (fl.size() > 1) a.push_back({&irgl_tuning::flags, fl});
   return a;
 }
 
@@ -39,13 +50,13 @@ std::vector<Axis> axes(bool with_delta, bool with_local) {
 
 // Coordinate descent; `measure` returns the median ms of one candidate (< 0: invalid).
 irgl_status irgl::tune_descend(const std::function<float(const irgl_tuning&)>& measure, irgl_tuning* best, float* best_ms,
-                                bool with_delta, bool with_local) {
+                                bool with_delta, bool with_local, bool with_diropt, uint32_t sms) {
   irgl_tuning cur = default_tuning();
   float cur_ms = measure(cur);
   if (cur_ms < 0) return fail(IRGL_ERR_CUDA, "autotune: default tuning failed: %s", g_last_error.c_str());
   for (int pass = 0; pass < 2; ++pass) {
     bool moved = false;
-    for (const Axis& ax : axes(with_delta, with_local)) {
+    for (const Axis& ax : axes(with_delta, with_local, with_diropt, sms)) {
       for (uint32_t v : ax.values) {
         if (cur.*(ax.field) == v) continue;
         irgl_tuning cand = cur;
@@ -124,7 +135,9 @@ irgl_status irgl_autotune(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uin
     }
     return median(ms);
   };
-  s = tune_descend(measure, best, best_ms, k == IRGL_SSSP, k == IRGL_BFS || k == IRGL_SSSP);
+  const bool diropt = k == IRGL_BFS && (g->in_row_ptr != nullptr || (g->flags & IRGL_SYMMETRIC));
+  s = tune_descend(measure, best, best_ms, k == IRGL_SSSP, k == IRGL_BFS || k == IRGL_SSSP, diropt,
+                   static_cast<uint32_t>(ctx->sm_count));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return s;

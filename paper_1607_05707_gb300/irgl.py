@@ -45,6 +45,8 @@ IRGL_TUNE_NO_SPLIT = 0x1
 IRGL_TUNE_DIROPT = 0x2
 IRGL_TUNE_BITMAP = 0x4
 IRGL_TUNE_NO_PACKED = 0x8
+IRGL_TUNE_NO_BCAST = 0x10
+IRGL_TUNE_THREAD_BIN = 0x20
 
 
 def IRGL_TUNE_LOCAL(k: int) -> int:

@@ -227,12 +227,15 @@ def test_trace_records_rounds(ctx):
     out, st = ctx.run("bfs", dg, srcs)
     t, a, o = trace(ctx)
     C.irgl_trace_enable(ctx.handle, 0)
-    assert len(t) == st["rounds"] + 1 == 128
+    # prologue record, one record per round, epilogue record
+    assert len(t) == st["rounds"] + 2 == 129
     assert (np.diff(t.astype(np.int64)) >= 0).all()
+    assert 0 < int(o[0]) < 10**9  # prologue duration (ns)
     # round r pops the r-th anti-diagonal of the 64x64 grid (from the corner): min(r+1, 127-r) vertices
     r = np.arange(0, 127)
-    np.testing.assert_array_equal(a[1:], np.minimum(r + 1, 127 - r))
-    assert o[-1] == 0
+    np.testing.assert_array_equal(a[1:-1], np.minimum(r + 1, 127 - r))
+    assert o[-2] == 0
+    assert a[-1] == 0xFFFFFFFF and o[-1] == 0xFFFFFFFF
     dg.close()
 
 
@@ -277,6 +280,45 @@ def test_grid_batch_matches_oracle(ctx, delta):
             np.testing.assert_array_equal(got, want, err_msg=f"query {q} ({k}) delta {delta} rep {rep}")
             if k == "bfs":
                 assert rounds == int(want[want != INF].max()) + 1
+    b.close()
+    for dg in loaded.values():
+        dg.close()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("tuning", [dict(flags=15 << 8), dict(flags=4 << 8, delta=512),
+                                    dict(flags=(15 << 8) | 0x20, cta_size=256, delta=64),
+                                    dict(flags=2 << 8, cta_size=1024, warp_thresh=2, cta_thresh=8)])
+def test_batch_sub_rounds_match_oracle(ctx, use_graph, tuning):
+    """CTA-local sub-rounds in the batched kernel (BFS as unit-weight relaxation,
+    a local pop clearing its round stamp): grids, meshes and R-MAT instances
+    mixed, with and without per-query near-far; every result equals the
+    oracle's and a grid BFS needs fewer global rounds than levels."""
+    from paper_1607_05707_gb300.api import Batch
+
+    inst = [(g, s, k) for g, s, k in inputs.workload_grid_batch(count=10, graphs=3, lo=64, hi=200)]
+    inst += [(g, s, k) for k, g, s in _instances()[:9] if k != "cc"]
+    m = inputs.mesh(90, 70, seed=5, del_frac=0.02, extra_frac=0.01, weights=True)
+    inst += [(m, np.array([0], np.uint32), "bfs"), (m, np.array([11], np.uint32), "sssp")]
+    loaded = {}
+    for g, _, _ in inst:
+        if id(g) not in loaded:
+            loaded[id(g)] = ctx.load(g)
+    b = Batch(ctx, 32)
+    for g, s, k in inst:
+        b.add(k, loaded[id(g)], s)
+    b.prepare(tuning, use_cuda_graph=use_graph)
+    for rep in range(2):
+        b.run()
+        for q, (g, s, k) in enumerate(inst):
+            got, rounds = b.result(q)
+            want = oracle.run(k, g, s)
+            np.testing.assert_array_equal(got, want, err_msg=f"query {q} ({k}) {tuning} rep {rep}")
+            if k == "bfs":
+                levels = int(want[want != INF].max()) + 1
+                assert 1 <= rounds <= levels
+                if g is m and (tuning["flags"] >> 8) >= 4:
+                    assert rounds < levels
     b.close()
     for dg in loaded.values():
         dg.close()

@@ -33,6 +33,10 @@ SCHEDULES = [
     dict(cta_size=256, flags=4 | 8),      # BFS visited bitmap, SSSP distances and stamps in two arrays
     dict(cta_size=1024, warp_thresh=1 << 30, cta_thresh=1 << 30, flags=8),  # two-array SSSP through the scan bin
     dict(cta_size=512, warp_thresh=4, cta_thresh=32, delta=8),    # near-far through small bins
+    dict(cta_size=128, flags=0x10),       # small frontiers through the bins and the big list as well
+    dict(cta_size=256, warp_thresh=4, cta_thresh=16, flags=0x10 | 8),  # the same, two-array SSSP
+    dict(cta_size=128, flags=0x20),       # lists of 1..4 edges walked by their own lane (thread bin)
+    dict(cta_size=512, warp_thresh=8, cta_thresh=64, flags=0x30, delta=16),  # thread bin, no broadcast, near-far
 ]
 
 
