@@ -480,11 +480,15 @@ def run_gpu(args, world, rank, local):
     if args.trace and rank == 0:
         C.irgl_trace_enable(ctx.handle, 1 << 16)
         for k in kernels:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
             ctx.iterate_async(k, dg, init(k, used[0]), out[k], tuning=ktune[k])
+            e1.record(stream)
             st = ctx.sync()
             t, a, o = C.irgl_trace_read(ctx.handle)
             print(f"# trace {k} source {srcs[used[0]]}: rounds={st['rounds']} total_us={(int(t[-1]) - int(t[0])) / 1e3:.1f}"
-                  f" prologue_us={int(o[0]) / 1e3:.2f}", file=sys.stderr)
+                  f" prologue_us={int(o[0]) / 1e3:.2f} event_us={1e3 * e0.elapsed_time(e1):.1f}", file=sys.stderr)
             for r in range(1, len(t)):
                 if int(a[r]) == INF and int(o[r]) == INF:
                     print(f"#  epilogue us {(int(t[r]) - int(t[r - 1])) / 1e3:9.2f}", file=sys.stderr)

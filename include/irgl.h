@@ -44,6 +44,8 @@ typedef int irgl_status;
 #define IRGL_ERR_NOT_READY (-9)       /* polled result not finished yet */
 #define IRGL_ERR_UNSUPPORTED (-10)    /* option not available for this kernel/mode */
 #define IRGL_ERR_LOCK_TIMEOUT (-11)   /* an Atomic section's lock wait hit its time limit */
+#define IRGL_ERR_TIME_LIMIT (-12)     /* a persistent launch ran past its wall-time limit (60 s by default;
+                                         test hook key 7 sets it in ms): the work did not converge in time */
 
 #define IRGL_INF 0xFFFFFFFFu
 
@@ -119,11 +121,27 @@ typedef struct {
                                     lowered by one atomicMin, and the distances are copied to the
                                     output at the end) */
 #define IRGL_TUNE_NO_BCAST 0x10u /* persistent BFS, SSSP and CC: run small-frontier rounds like the
-                                    others. By default a round whose frontier has at most 768 items
-                                    (and at most 2^20 / grid) skips the degree bins and the grid-wide
-                                    list of long adjacency lists: every CTA reads the whole frontier,
-                                    scans its degrees in shared memory and relaxes an equal share of
-                                    its edges (one grid barrier per round instead of two) */
+                                    others. By default, on a graph with an adjacency list at least as
+                                    long as the smaller degree threshold (known when the CSR was loaded
+                                    from host arrays or validated; else assumed), a round whose frontier
+                                    has at most 768 items (and at most 2^20 / grid) skips the degree bins
+                                    and the grid-wide list of long adjacency lists: every CTA reads the
+                                    whole frontier, scans its degrees in shared memory and relaxes an
+                                    equal share of its edges (one grid barrier per round instead of two) */
+#define IRGL_TUNE_NO_SMEM 0x40u /* persistent BFS, SSSP and CC: use the grid-wide kernels even when
+                                    the graph fits in one CTA's shared memory. By default a graph whose
+                                    CSR, values and two worklists fit the device's opt-in shared memory
+                                    per block (about 227 KB: some 4,000 vertices and 16,000 edges for
+                                    SSSP) runs the whole Iterate in one CTA of 1024 threads with every
+                                    access in shared memory and __syncthreads between the rounds; the
+                                    schedule flags (sub-rounds, near-far, bottom-up rounds, bins) do
+                                    not apply to it, and the stats report grid 1, CTA 1024 */
+#define IRGL_TUNE_DENSE 0x80u /* persistent BFS, and SSSP on packed words (no near-far, no
+                                    sub-rounds): a round whose frontier holds more than n / 8 items
+                                    looks at every vertex in id order and pops those the previous
+                                    round pushed (the round id in their packed word; for BFS, level
+                                    = the round), so row offsets are read in order and the adjacency
+                                    lists of neighbouring frontier vertices are neighbours in memory */
 #define IRGL_TUNE_THREAD_BIN 0x20u /* all kernels: the lane that popped an adjacency list of 1..4 edges
                                     walks it itself (no per-edge search or shuffle) instead of the warp's
                                     scan bin dealing it out with the other short lists. Off by default:
@@ -502,11 +520,15 @@ irgl_status irgl_msf(irgl_ctx* ctx, irgl_graph* g, irgl_mode mode, irgl_lock loc
  *          IRGL_ERR_BARRIER_TIMEOUT.
  *   key 3: override the capacity of the Iterate scratch worklists (0 = n).
  *   key 4: cap the big list of persistent Iterate launches (0 = default), so
- *          long lists beyond the cap take the CTA-bin path.
+ *          long lists beyond the cap take the warp-bin path.
  *   key 5: 1 = direction-optimising BFS runs every round bottom-up.
  *   key 6: minimum spanning forest: the lock of this component (vertex id;
  *          -1 = none) starts held and is never released, so its waits run
- *          out and the call returns IRGL_ERR_LOCK_TIMEOUT. */
+ *          out and the call returns IRGL_ERR_LOCK_TIMEOUT.
+ *   key 7: wall-time limit of persistent Iterate, batch and server launches in
+ *          milliseconds (0 = default 60 s); a launch past it stops at its next
+ *          round with IRGL_ERR_TIME_LIMIT (batches and servers read it when they
+ *          are prepared or created). */
 irgl_status irgl_debug_set(irgl_ctx* ctx, int key, int64_t value);
 
 #ifdef __cplusplus

@@ -32,6 +32,7 @@ CUDA_UNITS = [
     "irgl_api.cu",
     "irgl_k_single.cu",
     "irgl_k_launch.cu",
+    "irgl_k_smem.cu",
     "irgl_k_batch.cu",
     "irgl_batch.cu",
     "irgl_server.cu",

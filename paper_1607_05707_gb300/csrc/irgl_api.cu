@@ -49,6 +49,10 @@ DeviceGuard::~DeviceGuard() {
   if (prev_ != dev_) cudaSetDevice(prev_);
 }
 
+unsigned long long run_time_limit_ns(const irgl_ctx* ctx) {
+  return ctx->dbg_time_limit_ms ? ctx->dbg_time_limit_ms * 1000000ull : kRunTimeLimitNs;
+}
+
 uint32_t thread_bin(const irgl_tuning& t) { return (t.flags & IRGL_TUNE_THREAD_BIN) ? kThreadBin : 0u; }
 
 irgl_tuning default_tuning() {
@@ -94,6 +98,7 @@ irgl_status status_from_device(const DevStatus& s) {
     case DERR_BAD_ITEM: return fail(IRGL_ERR_INVALID_ARG, "a worklist item is not a vertex of the graph");
     case DERR_LOCK_TIMEOUT: return fail(IRGL_ERR_LOCK_TIMEOUT, "an Atomic section's lock wait exceeded its time limit");
     case DERR_MSF_ITERS: return fail(IRGL_ERR_CUDA, "Boruvka's algorithm did not converge");
+    case DERR_TIME_LIMIT: return fail(IRGL_ERR_TIME_LIMIT, "persistent launch ran past its time limit");
   }
   return fail(IRGL_ERR_CUDA, "unknown device error %u", s.err);
 }
@@ -271,13 +276,17 @@ KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tu
   p.tn.thread_max = thread_bin(t);
   p.max_rounds = 0xFFFFFFFFu;
   p.timeout_ns = ctx->dbg_timeout_us ? ctx->dbg_timeout_us * 1000ull : 2000000000ull;
+  p.time_limit_ns = run_time_limit_ns(ctx);
   p.skip_cta = -1;
   p.init_state = 1;
   p.trace = ctx->trace;
   p.trace_cap = ctx->trace_cap;
   p.big = (t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{ctx->big_e, ctx->big_off, ctx->big_cap};
   if (ctx->dbg_big_cap && p.big.cap > ctx->dbg_big_cap) p.big.cap = ctx->dbg_big_cap;
-  p.bcast = (t.flags & IRGL_TUNE_NO_BCAST) ? 0u : 1u;
+  // small-frontier rounds pay for their broadcast reads by skipping the big
+  // list: only graphs with lists long enough to go there use them
+  p.bcast = (!(t.flags & IRGL_TUNE_NO_BCAST) && g->max_deg >= std::min(t.warp_thresh, t.cta_thresh)) ? 1u : 0u;
+  p.dense_div = (t.flags & IRGL_TUNE_DENSE) ? 8u : 0u;
   if ((t.flags & IRGL_TUNE_DIROPT) && (g->in_row_ptr || (g->flags & IRGL_SYMMETRIC))) {
     p.in_row_ptr = g->in_row_ptr ? g->in_row_ptr : g->row_ptr;
     p.in_col = g->in_row_ptr ? g->in_col : g->col;
@@ -332,6 +341,7 @@ irgl_status irgl_ctx_create(int device, void* cuda_stream, irgl_ctx** out) {
   ctx->device = device;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->st, sizeof(DevStatus));
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->st_host, sizeof(DevStatus));
   if (e != cudaSuccess) {
@@ -352,6 +362,8 @@ irgl_status irgl_ctx_destroy(irgl_ctx* ctx) {
   cudaFree(ctx->ws_items[1]);
   cudaFree(ctx->ws_stamp);
   cudaFree(ctx->ws_vis);
+  cudaFree(ctx->ws_bu[0]);
+  cudaFree(ctx->ws_bu[1]);
   cudaFree(ctx->ws_ds);
   cudaFree(ctx->msf_buf);
   if (ctx->msf_host) cudaFreeHost(ctx->msf_host);
@@ -427,6 +439,7 @@ irgl_status irgl_debug_set(irgl_ctx* ctx, int key, int64_t value) {
     case 2: ctx->dbg_skip_cta = static_cast<int>(value); return IRGL_OK;
     case 3: ctx->dbg_cap = value > 0 ? static_cast<uint32_t>(value) : 0; return IRGL_OK;
     case 4: ctx->dbg_big_cap = value > 0 ? static_cast<uint32_t>(value) : 0; return IRGL_OK;
+    case 7: ctx->dbg_time_limit_ms = value > 0 ? static_cast<uint64_t>(value) : 0; return IRGL_OK;
     case 5: ctx->dbg_force_bottom_up = value > 0 ? 1u : 0u; return IRGL_OK;
     case 6: ctx->dbg_held_lock = value >= 0 ? static_cast<uint32_t>(value) : 0xFFFFFFFFu; return IRGL_OK;
   }
@@ -482,11 +495,14 @@ irgl_status irgl_csr_load(irgl_ctx* ctx, uint32_t n, uint64_t m, const uint32_t*
   DeviceGuard guard(ctx->device);
   const bool dev = (flags & IRGL_DEVICE_PTRS) != 0;
   int32_t max_w = 0;
+  uint32_t max_deg = 0xFFFFFFFFu;  // unknown unless the offsets are read on the host
   if (!dev) {
     irgl_status s = irgl_csr_validate(n, m, row_ptr, col, w, flags);
     if (s != IRGL_OK) return s;
     if (w)
       for (uint64_t e = 0; e < m; ++e) max_w = std::max(max_w, w[e]);
+    max_deg = 0;
+    for (uint32_t v = 0; v < n; ++v) max_deg = std::max(max_deg, row_ptr[v + 1] - row_ptr[v]);
   } else {
     if (!row_ptr || (m > 0 && !col)) return fail(IRGL_ERR_INVALID_ARG, "row_ptr/col is NULL");
     if ((reinterpret_cast<uintptr_t>(col) & 15u) || (w && (reinterpret_cast<uintptr_t>(w) & 15u)))
@@ -514,6 +530,8 @@ irgl_status irgl_csr_load(irgl_ctx* ctx, uint32_t n, uint64_t m, const uint32_t*
       if (flags & IRGL_VALIDATE) {
         irgl_status s = irgl_csr_validate(n, m, hr.data(), hc.data(), w ? hw.data() : nullptr, flags);
         if (s != IRGL_OK) return s;
+        max_deg = 0;
+        for (uint32_t v = 0; v < n; ++v) max_deg = std::max(max_deg, hr[v + 1] - hr[v]);
       }
       for (uint64_t e2 = 0; e2 < m && w; ++e2) {
         if (hw[e2] < 0) return fail(IRGL_ERR_INVALID_ARG, "negative weight at edge %llu", (unsigned long long)e2);
@@ -528,6 +546,7 @@ irgl_status irgl_csr_load(irgl_ctx* ctx, uint32_t n, uint64_t m, const uint32_t*
   g->m = m;
   g->flags = flags;
   g->max_w = max_w;
+  g->max_deg = max_deg;
   if (dev) {
     g->row_ptr = const_cast<uint32_t*>(row_ptr);
     g->col = const_cast<uint32_t*>(col);
@@ -785,6 +804,22 @@ irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workl
   p.max_rounds = max_rounds ? max_rounds : 0xFFFFFFFFu;
   if (vis) p.vis = ctx->ws_vis;
   if (packed) p.ds = ctx->ws_ds;
+  if (mode == IRGL_PERSISTENT && p.diropt != 0 && !use_local) {
+    // lists of the vertices each bottom-up round leaves open (the next one looks at those only)
+    if (g->n > ctx->ws_bu_n) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->ws_bu[0]);
+      cudaFree(ctx->ws_bu[1]);
+      ctx->ws_bu[0] = ctx->ws_bu[1] = nullptr;
+      ctx->ws_bu_n = 0;
+      cudaError_t e = cudaMalloc(&ctx->ws_bu[0], sizeof(uint32_t) * (size_t)g->n);
+      if (e == cudaSuccess) e = cudaMalloc(&ctx->ws_bu[1], sizeof(uint32_t) * (size_t)g->n);
+      if (e != cudaSuccess) return cuda_fail(e, "bottom-up list allocation");
+      ctx->ws_bu_n = g->n;
+    }
+    p.bu_list[0] = ctx->ws_bu[0];
+    p.bu_list[1] = ctx->ws_bu[1];
+  }
   if (use_local) {
     p.local_rounds = sub_rounds;
     p.diropt = 0;
@@ -795,6 +830,31 @@ irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workl
   irgl_stats local;
   std::memset(&local, 0, sizeof(local));
   local.cta_size = t.cta_size;
+
+  if (mode == IRGL_PERSISTENT && !(t.flags & IRGL_TUNE_NO_SMEM) && k != IRGL_CC_JUMP &&
+      ctx->smem_optin > static_cast<int>(kSmemStaticReserve) &&
+      smem_iterate_fits(op_of(k), g->n, g->m, static_cast<size_t>(ctx->smem_optin) - kSmemStaticReserve)) {
+    // the whole Iterate in one CTA, the graph in shared memory (schedule choices
+    // such as sub-rounds, near-far or bottom-up rounds do not apply to it)
+    p.skip_cta = -1;
+    cudaError_t e = launch_smem_iterate(op_of(k), p, g->m, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "shared-memory Iterate launch");
+    local.grid = 1;
+    local.cta_size = 1024;
+    local.launches = 1;
+    if (!sync) {
+      if (stats) *stats = local;
+      return IRGL_OK;
+    }
+    DevStatus st;
+    s = read_status(ctx, &st);
+    local.rounds = ctx->st_host->rounds;
+    local.last_out = ctx->st_host->last_out;
+    local.edges_scanned = ctx->st_host->edges;
+    if (s == IRGL_OK) cudaMemsetAsync(&ctx->st->edges, 0, sizeof(unsigned long long), ctx->stream);
+    if (stats) *stats = local;
+    return s;
+  }
 
   if (mode == IRGL_PERSISTENT) {
     const uint32_t grid = persistent_grid(ctx, op, t);

@@ -401,6 +401,7 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   b->bp.max_rounds = 0xFFFFFFFFu;
   b->bp.rounds_cap_is_error = 1;
   b->bp.timeout_ns = ctx->dbg_timeout_us ? ctx->dbg_timeout_us * 1000ull : 2000000000ull;
+  b->bp.time_limit_ns = run_time_limit_ns(ctx);
   b->bp.trace = ctx->trace;
   b->bp.trace_cap = ctx->trace_cap;
   b->bp.big = (t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{b->big_e, b->big_off, b->big_cap};
@@ -513,6 +514,7 @@ irgl_status irgl_batch_sync(irgl_batch* b, irgl_stats* stats) {
       case DERR_BARRIER_TIMEOUT: s = fail(IRGL_ERR_BARRIER_TIMEOUT, "grid barrier wait exceeded its time limit"); break;
       case DERR_MAX_ROUNDS: s = fail(IRGL_ERR_MAX_ROUNDS, "batch reached max_rounds with work left"); break;
       case DERR_BAD_ITEM: s = fail(IRGL_ERR_INVALID_ARG, "a worklist item is not a vertex of its graph"); break;
+      case DERR_TIME_LIMIT: s = fail(IRGL_ERR_TIME_LIMIT, "batched launch ran past its time limit"); break;
       default: s = fail(IRGL_ERR_CUDA, "unknown device error %u", st.err); break;
     }
     batch_reset_status(b);

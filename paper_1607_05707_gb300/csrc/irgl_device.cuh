@@ -57,6 +57,7 @@ enum : uint32_t {
   DERR_BAD_ITEM = 4,
   DERR_LOCK_TIMEOUT = 5,   // an Atomic section's lock wait hit the time limit
   DERR_MSF_ITERS = 6,      // more Boruvka iterations than a forest can need
+  DERR_TIME_LIMIT = 7,     // a persistent launch ran past its wall-time limit
 };
 
 // Device status block. Each contended family sits on its own 128-byte line.
@@ -106,7 +107,10 @@ struct alignas(128) DevStatus {
   // the out-worklist, and the sizes of the far lists (both triple-buffered)
   uint32_t qnear[3][32];
   uint32_t bfar_tail[3];
-  uint32_t pad8[29];
+  // direction-optimising BFS: sizes of the lists of vertices the bottom-up
+  // rounds left open (triple-buffered by bottom-up round)
+  uint32_t bu_n[3];
+  uint32_t pad8[26];
 };
 static_assert(sizeof(DevStatus) == 1664, "status layout");
 
@@ -154,6 +158,7 @@ struct KParams {
   Tune tn;
   uint32_t max_rounds;         // 0xFFFFFFFF = none
   unsigned long long timeout_ns;
+  unsigned long long time_limit_ns;  // wall time after which the launch stops with DERR_TIME_LIMIT (0 = none)
   int skip_cta;                // test hook: this CTA never reaches the first barrier
   int init_state;              // write the Iterate initial values in the prologue
   unsigned long long* trace;   // optional per-round trace: {end time ns, (in_n << 32) | out_n}
@@ -180,8 +185,15 @@ struct KParams {
   // its tiles a CTA expands what it pushed to its shared-memory stage, up to
   // this many more times, before flushing the rest to the out-worklist
   uint32_t local_rounds;
+  // direction-optimising BFS: two lists (n entries each) of the vertices a
+  // bottom-up round left unvisited although they have in-edges; the next
+  // bottom-up round looks at those only (nullptr: every vertex, every time)
+  uint32_t* bu_list[2];
   // rounds over small frontiers run without the big list (broadcast_round); 0 = off
   uint32_t bcast;
+  // a round whose frontier has more than n / dense_div items runs dense (every
+  // vertex in id order, popped if the previous round pushed it); 0 = never
+  uint32_t dense_div;
 };
 
 // Per-launch (one round) arguments.
@@ -227,6 +239,7 @@ struct BParams {
   uint32_t max_rounds;      // rounds per launch (an epoch); 0xFFFFFFFF = run to empty
   int rounds_cap_is_error;  // 1: hitting max_rounds is DERR_MAX_ROUNDS; 0: epoch end
   unsigned long long timeout_ns;
+  unsigned long long time_limit_ns;  // wall time after which the launch stops with DERR_TIME_LIMIT (0 = none)
   unsigned long long* trace;
   uint32_t trace_cap;
   BigList big;
@@ -245,6 +258,16 @@ struct BParams {
 };
 
 // ----------------------------------------------------------------------------- small helpers
+
+// Wall-time bound of a persistent launch: CTA 0 checks it at the start of a
+// round and sets the sticky error, which the next grid barrier publishes, so
+// every CTA leaves the round loop together; a run that would never converge
+// ends with a status instead of holding the GPU.
+__device__ __forceinline__ unsigned long long globaltimer_ns();
+__device__ __forceinline__ void check_time_limit(uint32_t* err, unsigned long long t0, unsigned long long limit) {
+  if (limit != 0 && blockIdx.x == 0 && threadIdx.x == 0 && globaltimer_ns() - t0 > limit)
+    atomicCAS(err, 0u, static_cast<uint32_t>(DERR_TIME_LIMIT));
+}
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -433,6 +456,7 @@ __device__ __forceinline__ void push1(Smem<CTA>& sm, const Out& out, bool p, uin
 template <int CTA>
 __device__ __forceinline__ void push4(Smem<CTA>& sm, const Out& out, uint32_t f, uint32_t v0, uint32_t v1,
                                       uint32_t v2, uint32_t v3) {
+  if (!__any_sync(kFull, f != 0u)) return;  // most strips push nothing: one vote, no scan
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t k = __popc(f);
   const uint32_t incl = warp_incl_scan(k);
@@ -642,6 +666,11 @@ struct RoundCtx {
   const uint32_t* local_items;    // a sub-round's items: a range of the CTA's stage (shared memory)
   const uint32_t* far_in;         // batched near-far: the far items waiting from earlier rounds
   uint32_t far_in_n;
+  // dense round (single query): the items are every vertex in id order and a
+  // vertex is popped only if the previous round pushed it (its packed word
+  // carries dense_id; BFS: its level is this round's); else 0
+  uint32_t dense = 0;
+  uint32_t dense_id = 0;
 };
 
 // The destination's current value as the operator reads it. BFS with the
@@ -684,7 +713,9 @@ __device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state
     // improvement stamps 0: see decide_n). BFS levels are lowered from INF.
     const uint32_t o = OP == OP_RUNTIME ? op_rt : OP;
     const uint32_t nd = o == OP_SSSP ? val + static_cast<uint32_t>(wt) : (o == OP_BFSR ? val + 1u : val);
-    if (o == OP_BFS ? cur != kInf : nd >= cur) return 0u;
+    // batched BFS under CTA-local sub-rounds is label-correcting (as in decide_n)
+    const bool first_only = o == OP_BFS && !(OP == OP_RUNTIME && rc.local_rounds != 0);
+    if (first_only ? cur != kInf : nd >= cur) return 0u;
     const bool far = OP == OP_SSSP && rc.limit != kInf && nd >= rc.limit;
     const unsigned long long old =
         atomicMin(rc.ds + sb + v, (static_cast<unsigned long long>(nd) << 32) | (far ? 0u : rc.dsr));
@@ -872,12 +903,14 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
       const uint32_t vv[4] = {c.x, c.y, c.z, c.w};
       const int32_t wv[4] = {ww.x, ww.y, ww.z, ww.w};
       const uint32_t ops[4] = {op, op, op, op};
-      const uint32_t zero[4] = {0u, 0u, 0u, 0u};
+      const uint32_t sbs[4] = {sb, sb, sb, sb};  // arena base of every edge's destination
       const uint32_t vals[4] = {val, val, val, val};
       uint32_t cc[4], rr[4], ndv[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) cc[k] = load_cur<OP>(rc, state, sb, vv[k]);
-      decide_n<OP, 4>(rc, state, stamp, ops, zero, vv, vals, wv, cc, 0xFu, rr, ndv);
+      // array bases plus per-edge arena offsets, as in every other bin (the
+      // packed words are indexed ds + sb + v)
+      decide_n<OP, 4>(rc, g.state, g.stamp, ops, sbs, vv, vals, wv, cc, 0xFu, rr, ndv);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (rr[k] == 1u) fn |= 1u << k;
@@ -968,9 +1001,26 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
     item = rc.local_items ? rc.local_items[idx] : (rc.in_items ? __ldcg(rc.in_items + idx) : idx);
     uint32_t u;
     g.decode(item, q, u);
-    if (u >= g.nverts(q)) {  // a caller-pushed item outside the graph: report and skip it
+    uint32_t dval = 0;
+    if (!V::kBatched && rc.dense) {
+      // dense round: vertex `item` is popped only if the previous round pushed it
+      if (kPackedOp<OP> && rc.ds != nullptr) {
+        const unsigned long long wd = __ldcg(rc.ds + item);
+        dval = static_cast<uint32_t>(wd >> 32);
+        valid = static_cast<uint32_t>(wd) == rc.dense_id && dval != kInf;
+      } else {
+        dval = __ldcg(g.state + item);
+        valid = OP == OP_BFS && dval + 1u == rc.bfs_val;
+      }
+    }
+    if (!valid) {
+    } else if (u >= g.nverts(q)) {  // a caller-pushed item outside the graph: report and skip it
       set_err(rc.out.err, DERR_BAD_ITEM);
       valid = false;
+    } else if (!V::kBatched && rc.dense) {
+      beg = __ldg(g.rowp(q) + u);
+      end = __ldg(g.rowp(q) + u + 1);
+      val = OP == OP_BFS ? rc.bfs_val : dval;
     } else {
       const uint32_t* rp = g.rowp(q);
       beg = __ldg(rp + u);
@@ -1531,13 +1581,14 @@ __device__ __forceinline__ void big_phase(const V& g, Smem<CTA>& sm, const Round
     unsigned long long pos = lo;
     while (pos < hi && i0 < n) {
       const uint32_t lim = min(32u, n - i0);
+      // offsets into the concatenation fit 32 bits (it has fewer than 2^32 edges)
       uint4 en = make_uint4(0, 0, 0, 0);
-      unsigned long long off = ~0ull;  // lanes past the window never match
+      uint32_t off = 0xFFFFFFFFu;  // lanes past the window never match
       if (lane < lim) {
         en = __ldcg(rc.big.e + i0 + lane);
-        off = __ldcg(rc.big.off + i0 + lane);
+        off = static_cast<uint32_t>(__ldcg(rc.big.off + i0 + lane));
       }
-      const unsigned long long last_end = off + (en.y - en.x);
+      const unsigned long long last_end = static_cast<unsigned long long>(off) + (en.y - en.x);
       const unsigned long long wend_all = __shfl_sync(kFull, last_end, lim - 1);
       const unsigned long long wend = wend_all < hi ? wend_all : hi;
       for (unsigned long long base = pos; base < wend; base += E * 32) {
@@ -1546,9 +1597,10 @@ __device__ __forceinline__ void big_phase(const V& g, Smem<CTA>& sm, const Round
 #pragma unroll
         for (uint32_t k = 0; k < E; ++k) {
           const unsigned long long e = base + k * 32 + lane;
-          const uint32_t own = warp_find<unsigned long long>(off, e < wend ? e : wend - 1, lim);
+          const uint32_t e32 = static_cast<uint32_t>(e < wend ? e : wend - 1);
+          const uint32_t own = warp_find<uint32_t>(off, e32, lim);
           const uint32_t ob = __shfl_sync(kFull, en.x, own);
-          const unsigned long long oo = __shfl_sync(kFull, off, own);
+          const uint32_t oo = __shfl_sync(kFull, off, own);
           oqs[k] = __shfl_sync(kFull, en.w, own);
           ov[k] = __shfl_sync(kFull, en.z, own);
           v[k] = 0;
@@ -1556,7 +1608,7 @@ __device__ __forceinline__ void big_phase(const V& g, Smem<CTA>& sm, const Round
           sb[k] = 0;
           op[k] = OP_BFS;
           if (e < wend) {
-            const uint32_t edge = ob + static_cast<uint32_t>(e - oo);
+            const uint32_t edge = ob + (e32 - oo);
             op[k] = g.op(oqs[k]);
             sb[k] = g.sbase(oqs[k]);
             v[k] = ld_adj(g.colp(oqs[k]) + edge);
@@ -1629,19 +1681,26 @@ __device__ __forceinline__ void init_smem(Smem<CTA>& sm) {
 // after that (in-lists longer than eight) is scanned by the whole warp, 64
 // in-edges per step, so one long list does not hold the warp for hundreds
 // of dependent steps.
+#ifndef IRGL_BOTTOM_UP_J
+#define IRGL_BOTTOM_UP_J 4
+#endif
 template <int CTA>
 __device__ __forceinline__ void bottom_up_round(const KParams& p, Smem<CTA>& sm, const RoundCtx& rc, uint32_t L,
-                                                uint32_t& edges) {
-  constexpr uint32_t J = 4;
+                                                uint32_t& edges, const uint32_t* cand, uint32_t cand_n,
+                                                uint32_t* rest, uint32_t* rest_n) {
+  constexpr uint32_t J = IRGL_BOTTOM_UP_J;  // vertices per thread per pass
   constexpr uint32_t kLaneSteps = 4;
   const uint32_t lane = threadIdx.x & 31;
-  for (uint32_t base = blockIdx.x * (CTA * J); base < p.n; base += gridDim.x * (CTA * J)) {
+  // candidates: the list the previous bottom-up round left (cand), else every vertex
+  const uint32_t nv = cand ? cand_n : p.n;
+  for (uint32_t base = blockIdx.x * (CTA * J); base < nv; base += gridDim.x * (CTA * J)) {
     uint32_t v[J], b[J], e[J], ob[J], oe[J];
-    bool open[J], found[J];
+    bool open[J], found[J], keep[J];
 #pragma unroll
     for (uint32_t j = 0; j < J; ++j) {
-      v[j] = base + j * CTA + threadIdx.x;
-      open[j] = v[j] < p.n && __ldcg(p.state + v[j]) == kInf;
+      const uint32_t i = base + j * CTA + threadIdx.x;
+      v[j] = i < nv ? (cand ? __ldcg(cand + i) : i) : 0u;
+      open[j] = i < nv && __ldcg(p.state + v[j]) == kInf;
       found[j] = false;
     }
 #pragma unroll
@@ -1652,6 +1711,7 @@ __device__ __forceinline__ void bottom_up_round(const KParams& p, Smem<CTA>& sm,
       ob[j] = open[j] ? __ldg(p.row_ptr + v[j]) : 0u;
       oe[j] = open[j] ? __ldg(p.row_ptr + v[j] + 1) : 0u;
       open[j] = open[j] && b[j] < e[j];
+      keep[j] = open[j];  // unvisited with in-edges: kept for the next bottom-up round unless found
     }
     for (uint32_t step = 0; step < kLaneSteps; ++step) {
       uint32_t c[J][2];
@@ -1706,16 +1766,47 @@ __device__ __forceinline__ void bottom_up_round(const KParams& p, Smem<CTA>& sm,
         }
       }
     }
+    // out-edges of the found vertices for the direction rule: a thread sum, a
+    // warp sum, one shared atomic per warp
+    uint32_t mf = 0, fmask = 0;
 #pragma unroll
     for (uint32_t j = 0; j < J; ++j) {
       if (found[j]) {
         __stcg(p.state + v[j], L + 1u);
         if (p.vis) atomicOr(p.vis + (v[j] >> 5), 1u << (v[j] & 31u));
-        atomicAdd(&sm.mf_cta, static_cast<unsigned long long>(oe[j] - ob[j]));
+        mf += oe[j] - ob[j];
+        fmask |= 1u << j;
       }
     }
 #pragma unroll
-    for (uint32_t j = 0; j < J; ++j) push1<CTA>(sm, rc.out, found[j], v[j]);
+    for (int o = 16; o > 0; o >>= 1) mf += __shfl_xor_sync(kFull, mf, o);
+    if (lane == 0 && mf) atomicAdd(&sm.mf_cta, static_cast<unsigned long long>(mf));
+#pragma unroll
+    for (uint32_t j = 0; j < J; j += 4)
+      push4<CTA>(sm, rc.out, (fmask >> j) & 15u, v[j], J > j + 1 ? v[j + 1 < J ? j + 1 : j] : 0u,
+                 J > j + 2 ? v[j + 2 < J ? j + 2 : j] : 0u, J > j + 3 ? v[j + 3 < J ? j + 3 : j] : 0u);
+    if (rest) {
+      // vertices still unvisited after all their in-edges: the next bottom-up round's candidates
+      uint32_t kmask = 0;
+#pragma unroll
+      for (uint32_t j = 0; j < J; ++j) kmask |= (keep[j] && !found[j] ? 1u : 0u) << j;
+      const uint32_t k = __popc(kmask);
+      const uint32_t incl = warp_incl_scan(k);
+      const uint32_t total = __shfl_sync(kFull, incl, 31);
+      if (total) {
+        uint32_t gb = 0;
+        if (lane == 31) gb = atomicAdd(rest_n, total);
+        gb = __shfl_sync(kFull, gb, 31);
+        uint32_t pos = gb + incl - k;
+#pragma unroll
+        for (uint32_t j = 0; j < J; ++j) {
+          if ((kmask >> j) & 1u) {
+            if (pos < p.n) __stcg(rest + pos, v[j]);
+            ++pos;
+          }
+        }
+      }
+    }
     if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
   }
   __syncthreads();
@@ -1841,6 +1932,7 @@ __device__ __forceinline__ void persistent_exit(Smem<CTA>& sm, DevStatus* st, bo
     st->far_tail[0] = st->far_tail[1] = 0;
     st->far_min[0] = st->far_min[1] = 0;
     st->mf[0] = st->mf[1] = st->mf[2] = 0;
+    st->bu_n[0] = st->bu_n[1] = st->bu_n[2] = 0;
     st->exit_count = 0;
   }
   __threadfence();
@@ -1937,13 +2029,19 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   // back top-down when the frontier shrinks below n / 18
   const bool dopt = OP == OP_BFS && p.diropt != 0 && p.in_row_ptr != nullptr;
   bool bottom_up = dopt && p.diropt == 2;  // test hook: every round bottom-up
+  uint32_t bu_k = 0;                       // bottom-up rounds run so far
   unsigned long long visited_edges = 0;
   uint32_t prev_n = init_n;
   uint32_t in_n = init_n;
   // small frontiers skip the big list (broadcast_round): BFS, SSSP and
   // min-label CC rounds (near-far included) without CTA-local sub-rounds
   const bool bcast = p.bcast != 0 && (OP == OP_BFS || OP == OP_SSSP || OP == OP_CC) && p.local_rounds == 0;
+  // dense rounds: BFS, and SSSP on packed words, without near-far or sub-rounds
+  const bool dense_ok = p.dense_div != 0 && !nf && p.local_rounds == 0 &&
+                        (OP == OP_BFS || (OP == OP_SSSP && p.ds != nullptr));
+  const unsigned long long t_run0 = p.time_limit_ns ? globaltimer_ns() : 0ull;
   for (uint32_t r = 0; ok; ++r) {
+    check_time_limit(&st->err, t_run0, p.time_limit_ns);
     uint32_t* const cur = (r & 1) ? p.items[1] : p.items[0];  // no dynamic index into the param struct
     uint32_t* const nxt = (r & 1) ? p.items[0] : p.items[1];
     RoundCtx rc;
@@ -1967,6 +2065,17 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     rc.dsr = r * (p.local_rounds + 1u) + 1u;  // room for the sub-rounds' ids
     rc.local_rounds = (OP == OP_SSSP || OP == OP_BFSR) ? p.local_rounds : 0u;
     rc.local_items = nullptr;
+    // dense round: a large frontier is popped in vertex order (coalesced row
+    // offsets, neighbouring adjacency lists) instead of worklist order
+    const bool small_round =
+        bcast && in_n <= kBcast && static_cast<unsigned long long>(in_n) * gridDim.x <= kBcastBudget;
+    if (dense_ok && r > 0 && !split && !(dopt && bottom_up) && !small_round &&
+        static_cast<unsigned long long>(in_n) * p.dense_div > p.n) {
+      rc.dense = 1;
+      rc.dense_id = rc.dsr - 1u;  // the previous round's id (no sub-rounds here)
+      rc.in_items = nullptr;
+      rc.in_n = p.n;
+    }
     const uint32_t ftarget = split ? (fb ^ 1u) : fb;  // far list this round pushes to
     rc.far_out = Out{ftarget ? p.far[1] : p.far[0], &st->far_tail[ftarget], p.far_cap, &st->err};
     if (threadIdx.x == 0) {
@@ -1985,9 +2094,18 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     if (split) {
       split_far<OP, CTA>(g, sm, rc, fb ? p.far[1] : p.far[0], far_n, lim_old, limit);
     } else if (dopt && bottom_up) {
+      // bottom-up round k reads the list round k - 1 left (count bu_n[(k - 1) % 3]) and
+      // writes list k & 1 (count bu_n[k % 3]); bu_n[(k + 1) % 3], last read in round
+      // k - 1, is cleared now for round k + 1
+      const bool lists = p.bu_list[0] != nullptr;
+      const uint32_t* cand = (lists && bu_k != 0) ? p.bu_list[(bu_k + 1) & 1] : nullptr;
+      const uint32_t cand_n = cand ? min(__ldcg(&st->bu_n[(bu_k + 2) % 3]), p.n) : 0u;
+      if (lists && blockIdx.x == 0 && threadIdx.x == 0) st->bu_n[(bu_k + 1) % 3] = 0;
       __syncthreads();
-      bottom_up_round<CTA>(p, sm, rc, r, edges);
-    } else if (bcast && in_n <= kBcast && static_cast<unsigned long long>(in_n) * gridDim.x <= kBcastBudget) {
+      bottom_up_round<CTA>(p, sm, rc, r, edges, cand, cand_n, lists ? p.bu_list[bu_k & 1] : nullptr,
+                           &st->bu_n[bu_k % 3]);
+      ++bu_k;
+    } else if (small_round) {
       broadcast_round<OP, CTA>(g, sm, rc, edges);
     } else {
       round_body<OP, CTA, RED_NONE>(g, sm, rc, edges, dummy_t, dummy_f);
@@ -2273,7 +2391,9 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
   trace_round(p.trace, p.trace_cap, 0, init_n, 0);
   uint32_t in_n = init_n;
   const uint32_t id_step = p.ds != nullptr ? p.local_rounds + 1u : 1u;
+  const unsigned long long t_run0 = p.time_limit_ns ? globaltimer_ns() : 0ull;
   for (uint32_t r = 0; ok; ++r) {
+    check_time_limit(&st->err, t_run0, p.time_limit_ns);
     RoundCtx rc;
     rc.in_n = in_n;
     const uint32_t b = (cur0 + r) & 1u;

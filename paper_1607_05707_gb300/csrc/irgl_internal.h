@@ -17,6 +17,7 @@ struct irgl_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
+  int smem_optin = 0;  // opt-in shared memory per block (bytes)
   irgl::DevStatus* st = nullptr;       // device status block
   irgl::DevStatus* st_host = nullptr;  // pinned mirror
   uint32_t* ws_items[2] = {nullptr, nullptr};  // Iterate scratch worklists
@@ -32,6 +33,8 @@ struct irgl_ctx {
   uint32_t* msf_buf = nullptr;   // minimum spanning forest workspace (status block + 14 arrays of msf_n)
   uint32_t msf_n = 0;
   void* msf_host = nullptr;      // pinned copy of its status block
+  uint32_t* ws_bu[2] = {nullptr, nullptr};  // direction-optimising BFS: open-vertex lists
+  uint32_t ws_bu_n = 0;
   uint32_t* ws_vis = nullptr;    // persistent BFS visited bitmap
   uint32_t ws_vis_words = 0;
   unsigned long long* ws_ds = nullptr;  // persistent SSSP packed (dist, round id) words
@@ -44,6 +47,7 @@ struct irgl_ctx {
   uint32_t trace_cap = 0;
   // test hooks
   uint64_t dbg_timeout_us = 0;
+  uint64_t dbg_time_limit_ms = 0;  // wall-time limit of persistent launches (0: the default)
   int dbg_skip_cta = -1;
   uint32_t dbg_cap = 0;
   uint32_t dbg_big_cap = 0;
@@ -61,6 +65,7 @@ struct irgl_graph {
   bool owns = false;
   int flags = 0;
   int32_t max_w = 0;
+  uint32_t max_deg = 0xFFFFFFFFu;  // largest out-degree (0xFFFFFFFF: not known)
   uint32_t* in_row_ptr = nullptr;  // in-edge CSR (IRGL_IN_EDGES), owned
   uint32_t* in_col = nullptr;
 };
@@ -88,6 +93,8 @@ irgl_status fail(irgl_status s, const char* fmt, ...);
 irgl_status cuda_fail(cudaError_t e, const char* what);
 irgl_tuning default_tuning();
 uint32_t thread_bin(const irgl_tuning& t);  // Tune::thread_max of a tuning
+constexpr unsigned long long kRunTimeLimitNs = 60ull * 1000000000ull;  // persistent launches: 60 s
+unsigned long long run_time_limit_ns(const irgl_ctx* ctx);
 irgl_status resolve_tuning(const irgl_tuning* in, irgl_tuning* out);
 irgl_status read_status(irgl_ctx* ctx, DevStatus* out);
 irgl_status status_from_device(const DevStatus& s);

@@ -31,6 +31,16 @@ cudaError_t launch_admit(const AdmitParams& a, uint32_t grid, cudaStream_t s);
 cudaError_t launch_extract_values(const unsigned long long* ds, uint32_t* out, uint64_t n, uint32_t grid,
                                   cudaStream_t s);
 
+// Iterate in one CTA with the graph in shared memory (BFS, SSSP, min-label CC):
+// bytes of dynamic shared memory it needs, whether that fits `limit` (the
+// device's opt-in per-block maximum less the kernel's static shared memory),
+// and the launch (one CTA of 1024 threads; the status block gets rounds,
+// out size, edges and errors like a persistent launch).
+size_t smem_iterate_bytes(uint32_t op, uint32_t n, uint64_t m);
+bool smem_iterate_fits(uint32_t op, uint32_t n, uint64_t m, size_t limit);
+cudaError_t launch_smem_iterate(uint32_t op, const KParams& p, uint64_t m, cudaStream_t s);
+constexpr size_t kSmemStaticReserve = 256;  // the kernel's own __shared__ counters, rounded up
+
 inline bool valid_cta(uint32_t cta) { return cta == 128 || cta == 256 || cta == 512 || cta == 1024; }
 
 }  // namespace irgl

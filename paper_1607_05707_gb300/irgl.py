@@ -27,6 +27,7 @@ IRGL_ERR_MAX_ROUNDS = -8
 IRGL_ERR_NOT_READY = -9
 IRGL_ERR_UNSUPPORTED = -10
 IRGL_ERR_LOCK_TIMEOUT = -11
+IRGL_ERR_TIME_LIMIT = -12
 
 IRGL_INF = 0xFFFFFFFF
 
@@ -47,6 +48,8 @@ IRGL_TUNE_BITMAP = 0x4
 IRGL_TUNE_NO_PACKED = 0x8
 IRGL_TUNE_NO_BCAST = 0x10
 IRGL_TUNE_THREAD_BIN = 0x20
+IRGL_TUNE_NO_SMEM = 0x40
+IRGL_TUNE_DENSE = 0x80
 
 
 def IRGL_TUNE_LOCAL(k: int) -> int:

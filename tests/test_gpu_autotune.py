@@ -27,7 +27,8 @@ def ctx():
 def _valid(t: dict) -> None:
     assert t["cta_size"] in (128, 256, 512, 1024)
     assert t["warp_thresh"] <= t["cta_thresh"]
-    assert t["flags"] in (0, 4 << 8, 15 << 8)
+    assert t["flags"] in (0, 4 << 8, 15 << 8, 2)  # sub-rounds, or direction-optimising BFS
+    assert t["max_blocks"] in (0, 1, 2, 8, 32) or t["max_blocks"] >= 100  # or one CTA per SM
 
 
 @pytest.mark.parametrize("kind,make,srcs", [

@@ -322,3 +322,29 @@ def test_batch_sub_rounds_match_oracle(ctx, use_graph, tuning):
     b.close()
     for dg in loaded.values():
         dg.close()
+
+
+@pytest.mark.parametrize("tuning", [dict(max_blocks=2, warp_thresh=4, cta_thresh=1024),
+                                    dict(max_blocks=2, warp_thresh=4, cta_thresh=1024, delta=64),
+                                    dict(max_blocks=3, cta_size=256, warp_thresh=8, cta_thresh=4096, flags=4 << 8)])
+def test_batch_warp_bin_matches_oracle(ctx, tuning):
+    """The warp bin of the batched kernel (lists of warp_thresh..cta_thresh edges,
+    used when a round's frontier is larger than the grid: a grid of two or three
+    CTAs makes every round that large) lowers each query's own packed words: all
+    results equal the oracle's, with and without near-far and sub-rounds."""
+    from paper_1607_05707_gb300.api import Batch
+
+    inst = [(k, g, s) for k, g, s in _instances() if k != "cc"]
+    graphs = [ctx.load(g) for _, g, _ in inst]
+    b = Batch(ctx, 64)
+    for (k, g, s), dg in zip(inst, graphs):
+        b.add(k, dg, s)
+    b.prepare(tuning)
+    for rep in range(2):
+        b.run()
+        for q, (k, g, s) in enumerate(inst):
+            got, _ = b.result(q)
+            np.testing.assert_array_equal(got, oracle.run(k, g, s), err_msg=f"query {q} ({k}) {tuning} rep {rep}")
+    b.close()
+    for dg in graphs:
+        dg.close()

@@ -36,6 +36,8 @@ SCHEDULES = [
     dict(cta_size=128, flags=0x10),       # small frontiers through the bins and the big list as well
     dict(cta_size=256, warp_thresh=4, cta_thresh=16, flags=0x10 | 8),  # the same, two-array SSSP
     dict(cta_size=128, flags=0x20),       # lists of 1..4 edges walked by their own lane (thread bin)
+    dict(cta_size=128, flags=0x80),       # large frontiers popped in vertex order (dense rounds)
+    dict(cta_size=512, warp_thresh=4, cta_thresh=16, flags=0x80 | 0x10),  # dense, no broadcast rounds
     dict(cta_size=512, warp_thresh=8, cta_thresh=64, flags=0x30, delta=16),  # thread bin, no broadcast, near-far
 ]
 
@@ -59,14 +61,27 @@ def run(ctx, kernel, g, dg, srcs, mode="persistent", tuning=None):
     return as_u32(out)[: g.n], st
 
 
+NO_SMEM = 0x40  # IRGL_TUNE_NO_SMEM: grid-wide kernels even for graphs that fit in shared memory
+
+
 def check(ctx, kernel, g, dg, srcs, mode="persistent", tuning=None):
-    got, st = run(ctx, kernel, g, dg, srcs, mode, tuning)
     want = oracle.run("cc" if kernel == "cc_jump" else kernel, g, srcs)
-    if not np.array_equal(got, want):
-        bad = np.flatnonzero(got != want)
-        raise AssertionError(f"{kernel}/{mode}/{tuning}: {bad.size} of {g.n} differ; first {bad[:8]} "
-                             f"got {got[bad[:8]]} want {want[bad[:8]]}")
-    return st
+    tunings = [tuning]
+    if mode == "persistent" and kernel != "cc_jump" and g.n <= 20000:
+        # small graphs run in one CTA with the graph in shared memory by default:
+        # check the grid-wide kernels on them as well
+        t2 = dict(tuning or {})
+        t2["flags"] = int(t2.get("flags", 0)) | NO_SMEM
+        tunings.append(t2)
+    st0 = None
+    for t in tunings:
+        got, st = run(ctx, kernel, g, dg, srcs, mode, t)
+        if not np.array_equal(got, want):
+            bad = np.flatnonzero(got != want)
+            raise AssertionError(f"{kernel}/{mode}/{t}: {bad.size} of {g.n} differ; first {bad[:8]} "
+                                 f"got {got[bad[:8]]} want {want[bad[:8]]}")
+        st0 = st if st0 is None else st0
+    return st0
 
 
 def tiny_graph(rng, n, p, symmetric):
@@ -486,6 +501,39 @@ def test_rmat20_bfs_direction_optimising_full(ctx):
     dg = ctx.load(g, validate=False, in_edges=True)
     for s in srcs:
         check(ctx, "bfs", g, dg, np.array([s], np.uint32), "persistent", dict(flags=2))
+    dg.close()
+
+
+def test_time_limit_stops_and_recovers(ctx):
+    """A persistent launch past its wall-time limit (test hook key 7, here 1 ms)
+    stops at its next round with IRGL_ERR_TIME_LIMIT instead of running on, and
+    the context is exact afterwards; the same for a batch."""
+    from paper_1607_05707_gb300 import irgl as C
+    from paper_1607_05707_gb300.api import Batch
+
+    g = inputs.mesh(300, 257, seed=9, del_frac=0.01, extra_frac=0.001, radius=8)  # min-label CC: ~500 rounds
+    dg = ctx.load(g)
+    ctx.debug_set(7, 1)
+    try:
+        with pytest.raises(C.IrglError) as ei:
+            ctx.run("cc", dg, None, tuning=dict(flags=NO_SMEM))
+        assert ei.value.status == C.IRGL_ERR_TIME_LIMIT
+        b = Batch(ctx, 4)
+        b.add("cc", dg)
+        b.prepare()
+        with pytest.raises(C.IrglError) as ei:
+            b.run()
+        assert ei.value.status == C.IRGL_ERR_TIME_LIMIT
+        b.close()
+    finally:
+        ctx.debug_set(7, 0)
+    check(ctx, "cc", g, dg, None, "persistent")
+    b = Batch(ctx, 4)
+    b.add("cc", dg)
+    b.prepare()
+    b.run()
+    np.testing.assert_array_equal(b.result(0)[0], oracle.cc(g.n, g.row_ptr, g.col))
+    b.close()
     dg.close()
 
 
