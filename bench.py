@@ -844,7 +844,8 @@ def run_batch(args, world, rank, local, embedded=False):
                            tuning={**ctx.default_tuning, **(tuning or {})}, autotuned=autotuned),
             "per_launch": {"gteps_wall": round(seq_gteps, 4), "gteps_device": round(seq_dev_gteps, 4),
                            "form": "same instances, one persistent launch each, host waits per query"},
-            "batched_vs_per_launch": round(value / seq_gteps, 3),
+            "batched_vs_per_launch": round(value / seq_dev_gteps, 3),
+            "batched_vs_per_launch_clock": "device (CUDA events) for both forms",
             "e2e": {"value": round(e2e, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(4 * sum(g.n for g, _, _ in inst))},
             "gpu_launches": (3 * info["waves"] + 1) * args.steps,

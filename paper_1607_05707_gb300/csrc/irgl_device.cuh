@@ -1598,7 +1598,16 @@ __device__ __forceinline__ void big_phase(const V& g, Smem<CTA>& sm, const Round
         for (uint32_t k = 0; k < E; ++k) {
           const unsigned long long e = base + k * 32 + lane;
           const uint32_t e32 = static_cast<uint32_t>(e < wend ? e : wend - 1);
-          const uint32_t own = warp_find<uint32_t>(off, e32, lim);
+          // the 32 edges of this step start at most one new list when the lists
+          // are at least 32 edges long (the usual case): two ballots find the
+          // owners; more list starts take the shuffle search
+          const uint32_t ef = static_cast<uint32_t>(base + k * 32 < wend ? base + k * 32 : wend - 1);
+          const uint32_t el = static_cast<uint32_t>(base + k * 32 + 31 < wend ? base + k * 32 + 31 : wend - 1);
+          const uint32_t o1 = __popc(__ballot_sync(kFull, off <= ef)) - 1u;
+          const uint32_t starts = __popc(__ballot_sync(kFull, off <= el)) - 1u - o1;
+          uint32_t own = o1;
+          if (starts == 1u) own += e32 >= __shfl_sync(kFull, off, o1 + 1u) ? 1u : 0u;
+          else if (starts > 1u) own = warp_find<uint32_t>(off, e32, lim);
           const uint32_t ob = __shfl_sync(kFull, en.x, own);
           const uint32_t oo = __shfl_sync(kFull, off, own);
           oqs[k] = __shfl_sync(kFull, en.w, own);
@@ -1690,15 +1699,23 @@ __device__ __forceinline__ void bottom_up_round(const KParams& p, Smem<CTA>& sm,
                                                 uint32_t* rest, uint32_t* rest_n) {
   constexpr uint32_t J = IRGL_BOTTOM_UP_J;  // vertices per thread per pass
   constexpr uint32_t kLaneSteps = 4;
+  constexpr uint32_t kChunk = 32 * J;       // vertices per warp pass
   const uint32_t lane = threadIdx.x & 31;
   // candidates: the list the previous bottom-up round left (cand), else every vertex
   const uint32_t nv = cand ? cand_n : p.n;
-  for (uint32_t base = blockIdx.x * (CTA * J); base < nv; base += gridDim.x * (CTA * J)) {
+  // The work per vertex varies with its in-list and where the first parent
+  // sits in it, so chunks of kChunk vertices are dealt out per warp: the
+  // first one by warp index, the rest from the round's grab counter (a
+  // static share left the last CTA of a round 2.4x slower than the first).
+  const uint32_t nchunks = (nv + kChunk - 1) / kChunk;
+  const uint32_t nwarps = gridDim.x * (CTA / 32);
+  for (uint32_t c = blockIdx.x * (CTA / 32) + (threadIdx.x >> 5); c < nchunks;) {
+    const uint32_t base = c * kChunk;
     uint32_t v[J], b[J], e[J], ob[J], oe[J];
     bool open[J], found[J], keep[J];
 #pragma unroll
     for (uint32_t j = 0; j < J; ++j) {
-      const uint32_t i = base + j * CTA + threadIdx.x;
+      const uint32_t i = base + j * 32 + lane;
       v[j] = i < nv ? (cand ? __ldcg(cand + i) : i) : 0u;
       open[j] = i < nv && __ldcg(p.state + v[j]) == kInf;
       found[j] = false;
@@ -1807,7 +1824,10 @@ __device__ __forceinline__ void bottom_up_round(const KParams& p, Smem<CTA>& sm,
         }
       }
     }
-    if (__syncthreads_or(sm.stage_n >= static_cast<uint32_t>(Smem<CTA>::kStage / 2))) flush_stage<CTA>(sm, rc.out);
+    // next chunk (pushes past the stage go straight to the out-worklist)
+    uint32_t nc = 0;
+    if (lane == 0) nc = nwarps + atomicAdd(rc.grab, 1u);
+    c = __shfl_sync(kFull, nc, 0);
   }
   __syncthreads();
   flush_stage<CTA>(sm, rc.out);

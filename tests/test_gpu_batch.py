@@ -217,6 +217,28 @@ def test_batch_config_sample(ctx):
     b.close()
 
 
+@pytest.mark.parametrize("wave_mb", [0, 16])
+def test_batch256_full_matches_oracle(ctx, wave_mb):
+    """The whole 256-instance batched SSSP workload (R-MAT scale 10..18, edge factor 8,
+    1-4 sources), one CUDA-graph replay, every instance equal to the oracle's Dijkstra:
+    in one wave, and in waves of 16 MB of packed state each (many launches)."""
+    from paper_1607_05707_gb300.api import Batch
+
+    inst = inputs.workload_batch(count=256)
+    graphs = [ctx.load(g, validate=False) for g, _ in inst]
+    b = Batch(ctx, 256)
+    for (g, s), dg in zip(inst, graphs):
+        b.add("sssp", dg, s)
+    b.prepare(use_cuda_graph=True, wave_bytes=(wave_mb << 20) if wave_mb else None)
+    b.run()
+    for q, (g, s) in enumerate(inst):
+        got, _ = b.result(q)
+        np.testing.assert_array_equal(got, oracle.sssp(g.n, g.row_ptr, g.col, g.w, s), err_msg=f"instance {q}")
+    b.close()
+    for dg in graphs:
+        dg.close()
+
+
 def test_trace_records_rounds(ctx):
     from paper_1607_05707_gb300 import irgl as C
     from paper_1607_05707_gb300.api import as_u32, trace
