@@ -528,7 +528,11 @@ irgl_status irgl_msf(irgl_ctx* ctx, irgl_graph* g, irgl_mode mode, irgl_lock loc
  *   key 7: wall-time limit of persistent Iterate, batch and server launches in
  *          milliseconds (0 = default 60 s); a launch past it stops at its next
  *          round with IRGL_ERR_TIME_LIMIT (batches and servers read it when they
- *          are prepared or created). */
+ *          are prepared or created).
+ *   key 8: 1 = persistent Iterate, batch and server rounds whose frontier is
+ *          smaller than one tile per CTA keep it in static per-CTA spans
+ *          instead of spreading it over every CTA (batches and servers read it
+ *          when they are prepared or run an epoch). */
 irgl_status irgl_debug_set(irgl_ctx* ctx, int key, int64_t value);
 
 #ifdef __cplusplus

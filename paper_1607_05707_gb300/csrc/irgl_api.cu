@@ -287,6 +287,7 @@ KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tu
   // list: only graphs with lists long enough to go there use them
   p.bcast = (!(t.flags & IRGL_TUNE_NO_BCAST) && g->max_deg >= std::min(t.warp_thresh, t.cta_thresh)) ? 1u : 0u;
   p.dense_div = (t.flags & IRGL_TUNE_DENSE) ? 8u : 0u;
+  p.spread = ctx->dbg_no_spread ? 0u : 1u;
   if ((t.flags & IRGL_TUNE_DIROPT) && (g->in_row_ptr || (g->flags & IRGL_SYMMETRIC))) {
     p.in_row_ptr = g->in_row_ptr ? g->in_row_ptr : g->row_ptr;
     p.in_col = g->in_row_ptr ? g->in_col : g->col;
@@ -440,6 +441,7 @@ irgl_status irgl_debug_set(irgl_ctx* ctx, int key, int64_t value) {
     case 3: ctx->dbg_cap = value > 0 ? static_cast<uint32_t>(value) : 0; return IRGL_OK;
     case 4: ctx->dbg_big_cap = value > 0 ? static_cast<uint32_t>(value) : 0; return IRGL_OK;
     case 7: ctx->dbg_time_limit_ms = value > 0 ? static_cast<uint64_t>(value) : 0; return IRGL_OK;
+    case 8: ctx->dbg_no_spread = value > 0 ? 1u : 0u; return IRGL_OK;
     case 5: ctx->dbg_force_bottom_up = value > 0 ? 1u : 0u; return IRGL_OK;
     case 6: ctx->dbg_held_lock = value >= 0 ? static_cast<uint32_t>(value) : 0xFFFFFFFFu; return IRGL_OK;
   }

@@ -402,6 +402,7 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   b->bp.rounds_cap_is_error = 1;
   b->bp.timeout_ns = ctx->dbg_timeout_us ? ctx->dbg_timeout_us * 1000ull : 2000000000ull;
   b->bp.time_limit_ns = run_time_limit_ns(ctx);
+  b->bp.spread = ctx->dbg_no_spread ? 0u : 1u;
   b->bp.trace = ctx->trace;
   b->bp.trace_cap = ctx->trace_cap;
   b->bp.big = (t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{b->big_e, b->big_off, b->big_cap};

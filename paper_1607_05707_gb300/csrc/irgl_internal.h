@@ -48,6 +48,7 @@ struct irgl_ctx {
   // test hooks
   uint64_t dbg_timeout_us = 0;
   uint64_t dbg_time_limit_ms = 0;  // wall-time limit of persistent launches (0: the default)
+  uint32_t dbg_no_spread = 0;      // 1: sub-grid frontiers stay in static per-CTA spans
   int dbg_skip_cta = -1;
   uint32_t dbg_cap = 0;
   uint32_t dbg_big_cap = 0;

@@ -601,6 +601,7 @@ bool server_step(irgl_server* s) {
     bp.rounds_cap_is_error = 0;
     bp.timeout_ns = 2000000000ull;
     bp.time_limit_ns = run_time_limit_ns(s->ctx);
+    bp.spread = s->ctx->dbg_no_spread ? 0u : 1u;
     bp.big = (s->t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{s->big_e, s->big_off, s->big_cap};
     bp.delta = s->blim ? s->t.delta : 0u;
     bp.blim = s->blim;
