@@ -97,6 +97,12 @@ typedef struct {
                              is pushed). CC with delta = 1 floods the smallest label first, so
                              each vertex mostly takes its final label once. Batches and servers:
                              per-query near-far for their SSSP queries (below) */
+  uint32_t defer_deg;     /* persistent SSSP with plain rounds (delta = 0, no sub-rounds): a popped
+                             vertex with at least defer_deg out-edges whose distance is above the
+                             smallest distance pushed for the round + defer_delta is pushed again
+                             instead of expanded, so long lists are mostly scanned once, near their
+                             final distance (0 = default 128; IRGL_TUNE_NO_DEFER turns it off) */
+  uint32_t defer_delta;   /* that margin (0 = default 2) */
 } irgl_tuning;
 
 #define IRGL_TUNE_NO_SPLIT 0x1u
@@ -142,6 +148,7 @@ typedef struct {
                                     round pushed (the round id in their packed word; for BFS, level
                                     = the round), so row offsets are read in order and the adjacency
                                     lists of neighbouring frontier vertices are neighbours in memory */
+#define IRGL_TUNE_NO_DEFER 0x1000u /* persistent SSSP: expand every popped vertex (no deferred long lists) */
 #define IRGL_TUNE_THREAD_BIN 0x20u /* all kernels: the lane that popped an adjacency list of 1..4 edges
                                     walks it itself (no per-edge search or shuffle) instead of the warp's
                                     scan bin dealing it out with the other short lists. Off by default:

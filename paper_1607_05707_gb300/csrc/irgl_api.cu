@@ -65,6 +65,8 @@ irgl_tuning default_tuning() {
   t.max_blocks = 0;
   t.flags = 0;
   t.delta = 0;
+  t.defer_deg = 128;
+  t.defer_delta = 2;
   return t;
 }
 
@@ -79,6 +81,8 @@ irgl_status resolve_tuning(const irgl_tuning* in, irgl_tuning* out) {
     d.max_blocks = in->max_blocks;
     d.flags = in->flags;
     d.delta = in->delta;
+    if (in->defer_deg) d.defer_deg = in->defer_deg;
+    if (in->defer_delta) d.defer_delta = in->defer_delta;
   }
   if (!valid_cta(d.cta_size)) return fail(IRGL_ERR_INVALID_ARG, "cta_size must be 128, 256, 512 or 1024");
   if (d.chunk > 64) return fail(IRGL_ERR_INVALID_ARG, "chunk must be <= 64");
@@ -806,6 +810,11 @@ irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workl
   p.max_rounds = max_rounds ? max_rounds : 0xFFFFFFFFu;
   if (vis) p.vis = ctx->ws_vis;
   if (packed) p.ds = ctx->ws_ds;
+  if (mode == IRGL_PERSISTENT && k == IRGL_SSSP && packed && !far && !use_local &&
+      !(t.flags & (IRGL_TUNE_NO_DEFER | IRGL_TUNE_DENSE))) {
+    p.defer_deg = t.defer_deg;
+    p.defer_delta = t.defer_delta;
+  }
   if (mode == IRGL_PERSISTENT && p.diropt != 0 && !use_local) {
     // lists of the vertices each bottom-up round leaves open (the next one looks at those only)
     if (g->n > ctx->ws_bu_n) {

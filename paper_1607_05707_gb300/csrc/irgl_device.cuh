@@ -102,7 +102,9 @@ struct alignas(128) DevStatus {
   uint32_t pad6[4];
   // direction-optimising BFS: out-edges of the vertices each round pushed (triple-buffered)
   unsigned long long mf[3];
-  uint32_t pad7[18];
+  // SSSP deferred expansion: ~(smallest distance pushed) per round (triple-buffered; 0 = none)
+  uint32_t pmin[3];
+  uint32_t pad7[15];
   // batched near-far: per-round bitmaps of the queries (by slot) that pushed to
   // the out-worklist, and the sizes of the far lists (both triple-buffered)
   uint32_t qnear[3][32];
@@ -196,6 +198,11 @@ struct KParams {
   uint32_t dense_div;
   // rounds whose frontier is below one tile per CTA spread it over the grid; 0 = off
   uint32_t spread;
+  // SSSP on packed words, plain rounds: a popped vertex of degree >= defer_deg
+  // whose distance exceeds the round's smallest pushed distance + defer_delta
+  // is pushed again instead of expanded (defer_deg 0: off)
+  uint32_t defer_deg;
+  uint32_t defer_delta;
 };
 
 // Per-launch (one round) arguments.
@@ -366,6 +373,7 @@ struct Smem {
   uint32_t pub_flags;                       // kRelBigFlag when the big list is pending
   unsigned long long pub_big;               // published big-list counter
   unsigned long long mf_cta;                // out-edges of the vertices this CTA pushed this round
+  uint32_t pmin_cta;                        // smallest distance this CTA pushed since its last report (SSSP)
   unsigned long long edges;
   uint8_t pushed[CTA];                      // ReduceAndReturn All: item pushed something
 };
@@ -676,6 +684,12 @@ struct RoundCtx {
   uint32_t dense = 0;
   uint32_t dense_id = 0;
   uint32_t spread = 0;  // persistent launches: a frontier below one tile per CTA is spread over the grid
+  // single-query SSSP deferred expansion: lists of >= defer_deg edges whose
+  // vertex is above defer_lim wait a round (kInf: none); pmin gathers the
+  // smallest distance pushed (shared memory), or nullptr
+  uint32_t defer_lim = kInf;
+  uint32_t defer_deg = 0;
+  uint32_t* pmin = nullptr;
 };
 
 // The destination's current value as the operator reads it. BFS with the
@@ -725,7 +739,11 @@ __device__ __forceinline__ uint32_t decide_route(uint32_t op_rt, uint32_t* state
     const unsigned long long old =
         atomicMin(rc.ds + sb + v, (static_cast<unsigned long long>(nd) << 32) | (far ? 0u : rc.dsr));
     if (nd >= static_cast<uint32_t>(old >> 32)) return 0u;
-    if (!far) return static_cast<uint32_t>(old) != rc.dsr ? 1u : 0u;
+    if (!far) {
+      const bool push = static_cast<uint32_t>(old) != rc.dsr;
+      if (OP == OP_SSSP && push && rc.pmin != nullptr) atomicMin(rc.pmin, nd);
+      return push ? 1u : 0u;
+    }
     nd_out = nd;
     return atomicExch(rc.far_stamp + v, rc.phase) != rc.phase ? 2u : 0u;
   }
@@ -785,6 +803,12 @@ __device__ __forceinline__ void decide_n(const RoundCtx& rc, uint32_t* state, ui
 #pragma unroll
     for (int k = 0; k < N; ++k)
       r[k] = (t[k] && nd[k] < static_cast<uint32_t>(old[k] >> 32) && static_cast<uint32_t>(old[k]) != rc.dsr) ? 1u : 0u;
+    if (OP == OP_SSSP && rc.pmin != nullptr) {
+      uint32_t mn = kInf;
+#pragma unroll
+      for (int k = 0; k < N; ++k) mn = r[k] ? min(mn, nd[k]) : mn;
+      if (mn != kInf) atomicMin(rc.pmin, mn);
+    }
     return;
   }
   if (OP == OP_SSSP && rc.ds != nullptr) {
@@ -1002,6 +1026,7 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
   const uint32_t wbase = tid & ~31u;
   bool valid = idx < rc.in_n;
   uint32_t q = 0, beg = 0, end = 0, val = 0, item = 0;
+  unsigned long long pw = 0;  // the popped packed word (single-query SSSP)
   if (valid) {
     item = rc.local_items ? rc.local_items[idx] : (rc.in_items ? __ldcg(rc.in_items + idx) : idx);
     uint32_t u;
@@ -1039,13 +1064,32 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
         // the level its out-edges assign, its own + 1)
         val = static_cast<uint32_t>(atomicAnd(rc.ds + item, 0xFFFFFFFF00000000ull) >> 32) +
               (OP == OP_RUNTIME && op == OP_BFS ? 1u : 0u);
-      else if (kPackedOp<OP> && rc.ds != nullptr && (OP != OP_RUNTIME || op != OP_BFS))
-        val = static_cast<uint32_t>(__ldcg(rc.ds + item) >> 32);
-      else if (op == OP_BFS)
+      else if (kPackedOp<OP> && rc.ds != nullptr && (OP != OP_RUNTIME || op != OP_BFS)) {
+        pw = __ldcg(rc.ds + item);
+        val = static_cast<uint32_t>(pw >> 32);
+      } else if (op == OP_BFS)
         val = !V::kBatched ? rc.bfs_val
                            : (rc.ds != nullptr ? static_cast<uint32_t>(__ldcg(rc.ds + item) >> 32) : __ldcg(g.state + item)) + 1u;
       else val = __ldcg(g.state + item);
     }
+  }
+  if constexpr (!V::kBatched && OP == OP_SSSP) {
+    // Deferred expansion of long lists: a vertex of degree >= defer_deg whose
+    // distance is above defer_lim (the smallest distance pushed for this round
+    // plus a margin) is likely to be lowered again before it is final, and each
+    // expansion of it rescans all its edges. It stays on the worklist instead:
+    // pushed again for the next round (once: the round id in its packed word),
+    // its distance counted in the round's smallest, so the smallest item of a
+    // round is never deferred and every vertex is expanded in the end.
+    bool again = false;
+    if (valid && rc.defer_lim != kInf && !rc.dense && rc.local_items == nullptr && end - beg >= rc.defer_deg &&
+        val > rc.defer_lim) {
+      again = stamp_pending(rc.ds + item, pw, rc.dsr);
+      if (again) atomicMin(rc.pmin, val);
+      valid = false;
+      beg = end = 0;
+    }
+    if (rc.defer_lim != kInf) push1<CTA>(sm, rc.out, again, item);
   }
   if constexpr (V::kBatched) {
     if (g.lim != nullptr) {
@@ -1690,6 +1734,7 @@ __device__ __forceinline__ void init_smem(Smem<CTA>& sm) {
     sm.flag = 0;
     sm.round_pushes = 0;
     sm.big_appended = 0;
+    sm.pmin_cta = kInf;
   }
   __syncthreads();
 }
@@ -1970,6 +2015,7 @@ __device__ __forceinline__ void persistent_exit(Smem<CTA>& sm, DevStatus* st, bo
     st->far_min[0] = st->far_min[1] = 0;
     st->mf[0] = st->mf[1] = st->mf[2] = 0;
     st->bu_n[0] = st->bu_n[1] = st->bu_n[2] = 0;
+    st->pmin[0] = st->pmin[1] = st->pmin[2] = 0;
     st->exit_count = 0;
   }
   __threadfence();
@@ -2076,6 +2122,9 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   // dense rounds: BFS, and SSSP on packed words, without near-far or sub-rounds
   const bool dense_ok = p.dense_div != 0 && !nf && p.local_rounds == 0 &&
                         (OP == OP_BFS || (OP == OP_SSSP && p.ds != nullptr));
+  // deferred expansion of long lists (SSSP on packed words, plain rounds)
+  const bool defer = OP == OP_SSSP && p.defer_deg != 0 && p.ds != nullptr && !nf && p.local_rounds == 0 &&
+                     p.dense_div == 0;
   const unsigned long long t_run0 = p.time_limit_ns ? globaltimer_ns() : 0ull;
   for (uint32_t r = 0; ok; ++r) {
     check_time_limit(&st->err, t_run0, p.time_limit_ns);
@@ -2103,6 +2152,16 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     rc.local_rounds = (OP == OP_SSSP || OP == OP_BFSR) ? p.local_rounds : 0u;
     rc.local_items = nullptr;
     rc.spread = p.spread;
+    if (defer && r > 0) {
+      // the smallest distance pushed for this round (complete at the last barrier)
+      const uint32_t pm = __ldcg(&st->pmin[r % 3]);
+      if (pm != 0u) {
+        const unsigned long long lim = static_cast<unsigned long long>(~pm) + p.defer_delta;
+        rc.defer_lim = lim < kInf ? static_cast<uint32_t>(lim) : kInf;
+        rc.defer_deg = p.defer_deg;
+      }
+    }
+    rc.pmin = defer ? &sm.pmin_cta : nullptr;
     // dense round: a large frontier is popped in vertex order (coalesced row
     // offsets, neighbouring adjacency lists) instead of worklist order
     const bool small_round =
@@ -2128,6 +2187,9 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
       // mf[(r + 2) % 3] is still being read by CTAs that just left the last
       // barrier; mf[(r + 1) % 3] was read by every CTA before it arrived there
       if (dopt && blockIdx.x == 0) st->mf[(r + 1) % 3] = 0;
+      // pmin[(r + 1) % 3] gathers this round's pushes; pmin[(r + 2) % 3] was
+      // read at the start of the last round, before its barrier
+      if (defer && blockIdx.x == 0) st->pmin[(r + 2) % 3] = 0;
     }
     if (split) {
       split_far<OP, CTA>(g, sm, rc, fb ? p.far[1] : p.far[0], far_n, lim_old, limit);
@@ -2153,6 +2215,10 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
       sm.mf_cta = 0;
     }
     if (nf && threadIdx.x == 0 && sm.far_min_cta != kInf) atomicMax(&st->far_min[ftarget], ~sm.far_min_cta);
+    if (defer && threadIdx.x == 0 && sm.pmin_cta != kInf) {
+      atomicMax(&st->pmin[(r + 1) % 3], ~sm.pmin_cta);
+      sm.pmin_cta = kInf;
+    }
     ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns, !split && p.big.cap != 0);
     if (!ok) break;
     if (sm.pub_flags & kRelBigFlag) {
@@ -2161,6 +2227,10 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
       if (dopt && threadIdx.x == 0 && sm.mf_cta) {
         atomicAdd(&st->mf[r % 3], sm.mf_cta);
         sm.mf_cta = 0;
+      }
+      if (defer && threadIdx.x == 0 && sm.pmin_cta != kInf) {
+        atomicMax(&st->pmin[(r + 1) % 3], ~sm.pmin_cta);
+        sm.pmin_cta = kInf;
       }
       ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
       if (!ok) break;

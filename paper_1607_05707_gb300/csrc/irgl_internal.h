@@ -112,7 +112,7 @@ uint32_t op_of(irgl_kernel k);
 KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tuning& t);
 irgl_status tune_descend(const std::function<float(const irgl_tuning&)>& measure, irgl_tuning* best, float* best_ms,
                          bool with_delta = false, bool with_local = false, bool with_diropt = false,
-                         uint32_t sms = 0);
+                         uint32_t sms = 0, bool with_defer = false);
 
 }  // namespace irgl
 

@@ -21,7 +21,7 @@ struct Axis {
   std::vector<uint32_t> values;
 };
 
-std::vector<Axis> axes(bool with_delta, bool with_local, bool with_diropt, uint32_t sms) {
+std::vector<Axis> axes(bool with_delta, bool with_local, bool with_diropt, uint32_t sms, bool with_defer) {
   std::vector<Axis> a = {
       {&irgl_tuning::cta_size, {128, 256, 512, 1024}},
       {&irgl_tuning::cta_thresh, {32, 64, 128, 256, 512, 1024, 4096}},
@@ -34,6 +34,11 @@ std::vector<Axis> axes(bool with_delta, bool with_local, bool with_diropt, uint3
   // at all (the barrier's occupancy bound of Sec. 3.4 is an upper bound only)
   if (sms) a.push_back({&irgl_tuning::max_blocks, {0, 1, 2, 8, 32, sms}});
   if (with_delta) a.push_back({&irgl_tuning::delta, {0, 16, 32, 64, 128, 256, 512, 1024}});
+  // deferred expansion of long lists (single-query SSSP): degree bound and margin
+  if (with_defer) {
+    a.push_back({&irgl_tuning::defer_deg, {32, 64, 128, 256, 1024, 1u << 30}});
+    a.push_back({&irgl_tuning::defer_delta, {1, 2, 4, 8, 16}});
+  }
   // the flags the search sets (the defaults have none): CTA-local sub-rounds
   // and, when the graph has in-edges, direction-optimising BFS
   std::vector<uint32_t> fl = {0};
@@ -50,13 +55,13 @@ std::vector<Axis> axes(bool with_delta, bool with_local, bool with_diropt, uint3
 
 // Coordinate descent; `measure` returns the median ms of one candidate (< 0: invalid).
 irgl_status irgl::tune_descend(const std::function<float(const irgl_tuning&)>& measure, irgl_tuning* best, float* best_ms,
-                                bool with_delta, bool with_local, bool with_diropt, uint32_t sms) {
+                                bool with_delta, bool with_local, bool with_diropt, uint32_t sms, bool with_defer) {
   irgl_tuning cur = default_tuning();
   float cur_ms = measure(cur);
   if (cur_ms < 0) return fail(IRGL_ERR_CUDA, "autotune: default tuning failed: %s", g_last_error.c_str());
   for (int pass = 0; pass < 2; ++pass) {
     bool moved = false;
-    for (const Axis& ax : axes(with_delta, with_local, with_diropt, sms)) {
+    for (const Axis& ax : axes(with_delta, with_local, with_diropt, sms, with_defer)) {
       for (uint32_t v : ax.values) {
         if (cur.*(ax.field) == v) continue;
         irgl_tuning cand = cur;
@@ -137,7 +142,7 @@ irgl_status irgl_autotune(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uin
   };
   const bool diropt = k == IRGL_BFS && (g->in_row_ptr != nullptr || (g->flags & IRGL_SYMMETRIC));
   s = tune_descend(measure, best, best_ms, k == IRGL_SSSP, k == IRGL_BFS || k == IRGL_SSSP, diropt,
-                   static_cast<uint32_t>(ctx->sm_count));
+                   static_cast<uint32_t>(ctx->sm_count), k == IRGL_SSSP);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return s;

@@ -50,6 +50,7 @@ IRGL_TUNE_NO_BCAST = 0x10
 IRGL_TUNE_THREAD_BIN = 0x20
 IRGL_TUNE_NO_SMEM = 0x40
 IRGL_TUNE_DENSE = 0x80
+IRGL_TUNE_NO_DEFER = 0x1000
 
 
 def IRGL_TUNE_LOCAL(k: int) -> int:
@@ -70,6 +71,8 @@ class irgl_tuning(ctypes.Structure):
         ("max_blocks", c_uint32),
         ("flags", c_uint32),
         ("delta", c_uint32),
+        ("defer_deg", c_uint32),
+        ("defer_delta", c_uint32),
     ]
 
     def as_dict(self) -> dict:

@@ -39,6 +39,9 @@ SCHEDULES = [
     dict(cta_size=128, flags=0x80),       # large frontiers popped in vertex order (dense rounds)
     dict(cta_size=512, warp_thresh=4, cta_thresh=16, flags=0x80 | 0x10),  # dense, no broadcast rounds
     dict(cta_size=512, warp_thresh=8, cta_thresh=64, flags=0x30, delta=16),  # thread bin, no broadcast, near-far
+    dict(cta_size=256, defer_deg=1, defer_delta=1),   # SSSP: any vertex above the round's smallest + 1 waits
+    dict(cta_size=128, warp_thresh=4, cta_thresh=16, defer_deg=16, defer_delta=8),  # deferred lists, small bins
+    dict(cta_size=512, flags=0x1000),     # SSSP expands every pop (no deferred long lists)
 ]
 
 
