@@ -67,6 +67,7 @@ struct irgl_batch {
   uint32_t* far_items[2] = {nullptr, nullptr};  // near-far (tuning delta != 0): far lists
   uint32_t* far_stamp = nullptr;      //   arena: round id of the far list a vertex was last put on
   uint32_t* blim = nullptr;           //   per query: its limit
+  uint32_t* dmin = nullptr;           // deferred expansion: 3 x kMaxBatchQueries smallest pushed distances
   uint32_t* qfirst_host = nullptr;
   uint64_t wave_bytes = 0;            // 0: one wave
   std::vector<Wave> waves;
@@ -217,6 +218,8 @@ irgl_status irgl_batch_create(irgl_ctx* ctx, uint32_t max_queries, irgl_batch** 
   }
   if (e == cudaSuccess) e = cudaMalloc(&b->st, sizeof(DevStatus));
   if (e == cudaSuccess) e = cudaMallocHost(&b->st_host, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaMalloc(&b->dmin, sizeof(uint32_t) * 3 * kMaxBatchQueries);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->dmin, 0, sizeof(uint32_t) * 3 * kMaxBatchQueries, b->stream);
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
   if (e != cudaSuccess) {
@@ -234,6 +237,7 @@ irgl_status irgl_batch_destroy(irgl_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   batch_free_device(b);
   cudaFree(b->st);
+  cudaFree(b->dmin);
   if (b->st_host) cudaFreeHost(b->st_host);
   if (b->ev[0]) cudaEventDestroy(b->ev[0]);
   if (b->ev[1]) cudaEventDestroy(b->ev[1]);
@@ -414,6 +418,12 @@ irgl_status irgl_batch_prepare(irgl_batch* b, const irgl_tuning* tin, int use_cu
   b->bp.far_stamp = b->far_stamp;
   b->bp.local_rounds = b->ds ? (t.flags >> 8) & 15u : 0u;
   b->id_step = b->bp.local_rounds + 1u;
+  if (b->ds && !nf && b->bp.local_rounds == 0 && !(t.flags & IRGL_TUNE_NO_DEFER)) {
+    // deferred expansion of long lists for the SSSP queries
+    b->bp.dmin = b->dmin;
+    b->bp.defer_deg = t.defer_deg;
+    b->bp.defer_delta = t.defer_delta;
+  }
   b->aps.clear();
   for (const Wave& wv : b->waves) {
     AdmitParams ap{};
@@ -554,7 +564,7 @@ irgl_status irgl_batch_autotune(irgl_batch* b, uint32_t reps, irgl_tuning* best,
   };
   bool has_sssp = false;  // near-far delta is searched when the batch holds SSSP queries
   for (const BQuery& q : b->qs) has_sssp |= q.op == IRGL_SSSP;
-  irgl_status s = tune_descend(measure, best, best_ms, has_sssp, true);
+  irgl_status s = tune_descend(measure, best, best_ms, has_sssp, true, false, 0, has_sssp);
   if (s != IRGL_OK) return s;
   // then the wave budget: a quarter, half (the default) and all of the L2, and one wave
   int l2 = 0;

@@ -266,6 +266,12 @@ struct BParams {
   uint32_t local_rounds;
   // rounds whose frontier is below one tile per CTA spread it over the grid; 0 = off
   uint32_t spread;
+  // deferred expansion of long lists for SSSP queries (plain rounds): three
+  // buffers of kMaxBatchQueries words, ~(smallest distance a query pushed in a
+  // round) by slot; nullptr = off
+  uint32_t* dmin;
+  uint32_t defer_deg;
+  uint32_t defer_delta;
 };
 
 // ----------------------------------------------------------------------------- small helpers
@@ -559,6 +565,7 @@ struct SingleView {
   __device__ __forceinline__ uint32_t sbase(uint32_t) const { return 0u; }
   __device__ __forceinline__ void decode(uint32_t item, uint32_t& q, uint32_t& u) const { q = 0; u = item; }
   __device__ __forceinline__ void mark(uint32_t, uint32_t) const {}
+  __device__ __forceinline__ uint32_t slot(uint32_t) const { return 0u; }
 };
 
 // Many queries over many graphs; op taken per query at run time.
@@ -585,6 +592,7 @@ struct BatchView {
   }
   __device__ __forceinline__ uint32_t sbase(uint32_t q) const { return sbases[q]; }
   __device__ __forceinline__ uint32_t nverts(uint32_t q) const { return __ldg(&desc[q].n); }
+  __device__ __forceinline__ uint32_t slot(uint32_t q) const { return __ldg(&desc[q].slot); }
   __device__ __forceinline__ void decode(uint32_t item, uint32_t& q, uint32_t& u) const {
     uint32_t lo = 0, hi = nq - 1;
     while (lo < hi) {
@@ -690,7 +698,23 @@ struct RoundCtx {
   uint32_t defer_lim = kInf;
   uint32_t defer_deg = 0;
   uint32_t* pmin = nullptr;
+  // batched form: per-slot smallest pushed distances of the last round (limits
+  // of this one; nullptr: no deferral) and of this round (nullptr: not noted)
+  const uint32_t* bdmin_cur = nullptr;
+  uint32_t* bdmin_next = nullptr;
+  uint32_t defer_delta = 0;
 };
+
+// Batched deferred expansion: lanes that pushed SSSP distances for the same
+// query slot combine their smallest into one atomic on that slot's word of
+// the round's buffer (stored complemented, so 0 means nothing pushed). Every
+// lane of the warp calls it; mn = kInf: nothing to note.
+__device__ __forceinline__ void note_pushes(uint32_t* next, uint32_t slot, uint32_t mn) {
+  const uint32_t key = mn != kInf ? slot : 0xFFFFFFFFu;
+  const unsigned grp = __match_any_sync(kFull, key);
+  const uint32_t gm = __reduce_min_sync(grp, mn);
+  if (key != 0xFFFFFFFFu && (threadIdx.x & 31u) == static_cast<uint32_t>(__ffs(grp) - 1)) atomicMax(next + slot, ~gm);
+}
 
 // The destination's current value as the operator reads it. BFS with the
 // visited bitmap: the bit is read through L1 (a 128 KB bitmap of 2^20 vertices
@@ -922,7 +946,7 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
   scalar(beg + rank, a);
   for (uint32_t base = a; base < b; base += 4u * GROUP) {
     const uint32_t e = base + 4u * rank;
-    uint32_t fn = 0, ff = 0, dmin = kInf;
+    uint32_t fn = 0, ff = 0, dmin = kInf, pmn = kInf;
     uint4 c = make_uint4(0, 0, 0, 0);
     if (e < b) {
       c = ld_adj4(reinterpret_cast<const uint4*>(col + e));
@@ -942,7 +966,10 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
       decide_n<OP, 4>(rc, g.state, g.stamp, ops, sbs, vv, vals, wv, cc, 0xFu, rr, ndv);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        if (rr[k] == 1u) fn |= 1u << k;
+        if (rr[k] == 1u) {
+          fn |= 1u << k;
+          pmn = min(pmn, ndv[k]);
+        }
         if (kNearFarOp<OP> && rr[k] == 2u) {
           ff |= 1u << k;
           dmin = min(dmin, ndv[k]);
@@ -951,6 +978,9 @@ __device__ __forceinline__ bool group_edges(const V& g, Smem<CTA>& sm, const Rou
     }
     push4<CTA>(sm, rc.out, fn, sb + c.x, sb + c.y, sb + c.z, sb + c.w);
     if (kNearFarOp<OP>) push_far4<CTA>(sm, rc.far_out, ff, sb + c.x, sb + c.y, sb + c.z, sb + c.w, dmin);
+    if constexpr (V::kBatched) {
+      if (rc.bdmin_next != nullptr) note_pushes(rc.bdmin_next, g.slot(q), op == OP_SSSP ? pmn : kInf);
+    }
     any |= (fn | ff) != 0;
     if (GROUP == CTA) {
       // the predicate is taken at the barrier, when every warp's pushes are in
@@ -1090,6 +1120,26 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
       beg = end = 0;
     }
     if (rc.defer_lim != kInf) push1<CTA>(sm, rc.out, again, item);
+  }
+  if constexpr (V::kBatched) {
+    // the same for SSSP queries of a batch, each against its own smallest
+    // pushed distance of the last round (its slot's word; 0: none noted)
+    bool again = false;
+    if (rc.bdmin_cur != nullptr && valid && rc.local_items == nullptr && end - beg >= rc.defer_deg &&
+        g.op(q) == OP_SSSP) {
+      const uint32_t sl = g.slot(q);
+      const uint32_t pm = __ldcg(rc.bdmin_cur + sl);
+      if (pm != 0u && static_cast<unsigned long long>(val) > static_cast<unsigned long long>(~pm) + rc.defer_delta) {
+        again = stamp_pending(rc.ds + item, pw, rc.dsr);
+        if (again) {
+          atomicMax(rc.bdmin_next + sl, ~val);
+          g.mark(q, rc.ep);
+        }
+        valid = false;
+        beg = end = 0;
+      }
+    }
+    if (rc.bdmin_cur != nullptr) push1<CTA>(sm, rc.out, again, item);
   }
   if constexpr (V::kBatched) {
     if (g.lim != nullptr) {
@@ -1275,6 +1325,13 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
       if (r != 0u) {
         if (RED == RED_ALL) sm.pushed[wbase + own[k]] = 1;
         if (V::kBatched) g.mark(oqs[k], rc.ep);
+      }
+    }
+    if constexpr (V::kBatched) {
+      if (rc.bdmin_next != nullptr) {
+#pragma unroll
+        for (uint32_t k = 0; k < E; ++k)
+          note_pushes(rc.bdmin_next, g.slot(oqs[k]), (rr[k] == 1u && op[k] == OP_SSSP) ? ndv[k] : kInf);
       }
     }
     push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
@@ -1701,6 +1758,13 @@ __device__ __forceinline__ void big_phase(const V& g, Smem<CTA>& sm, const Round
             dmin = min(dmin, ndv[k]);
           }
           if (V::kBatched && r != 0u) g.mark(oqs[k], rc.ep);
+        }
+        if constexpr (V::kBatched) {
+          if (rc.bdmin_next != nullptr) {
+#pragma unroll
+            for (uint32_t k = 0; k < E; ++k)
+              note_pushes(rc.bdmin_next, g.slot(oqs[k]), (rr[k] == 1u && op[k] == OP_SSSP) ? ndv[k] : kInf);
+          }
         }
         push4<CTA>(sm, rc.out, f, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3]);
         if (kNearFarOp<OP>) push_far4<CTA>(sm, rc.far_out, ff, sb[0] + v[0], sb[1] + v[1], sb[2] + v[2], sb[3] + v[3], dmin);
@@ -2457,6 +2521,8 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
   // near-far (SSSP queries): limits in shared memory, advanced by delta after
   // every round in which the query pushed nothing to the out-worklist
   const bool nf = p.delta != 0 && p.ds != nullptr;
+  // deferred expansion of long lists (SSSP queries, packed words, plain rounds)
+  const bool bdefer = p.dmin != nullptr && p.defer_deg != 0 && p.ds != nullptr && !nf && p.local_rounds == 0;
   const uint32_t fcur0 = nf ? (__ldcg(p.cont + 2) & 1u) : 0u;
   uint32_t far_n = nf ? min(__ldcg(p.cont + 3), p.far_cap) : 0u;
   if (nf)
@@ -2526,6 +2592,19 @@ __device__ __forceinline__ void iterate_batch(const BParams& p, BatchSmem<CTA>& 
     rc.local_rounds = p.ds != nullptr ? p.local_rounds : 0u;
     rc.local_items = nullptr;
     rc.spread = p.spread;
+    if (bdefer) {
+      // round r reads the words round r - 1 noted, notes into (r + 1) % 3, and
+      // clears (r + 2) % 3 (read in round r - 1); the first rounds of a launch
+      // neither note into an uncleared buffer nor read one
+      if (r >= 2) rc.bdmin_cur = p.dmin + (r % 3u) * kMaxBatchQueries;
+      if (r >= 1) rc.bdmin_next = p.dmin + ((r + 1u) % 3u) * kMaxBatchQueries;
+      rc.defer_deg = p.defer_deg;
+      rc.defer_delta = p.defer_delta;
+      if (blockIdx.x == 0) {
+        uint32_t* clr = p.dmin + ((r + 2u) % 3u) * kMaxBatchQueries;
+        for (uint32_t i = threadIdx.x; i < static_cast<uint32_t>(kMaxBatchQueries); i += CTA) clr[i] = 0u;
+      }
+    }
     rc.far_in = nullptr;
     rc.far_in_n = 0;
     if (nf) {

@@ -370,3 +370,29 @@ def test_batch_warp_bin_matches_oracle(ctx, tuning):
     b.close()
     for dg in graphs:
         dg.close()
+
+
+@pytest.mark.parametrize("tuning", [dict(defer_deg=1, defer_delta=1), dict(cta_size=256, defer_deg=8, defer_delta=4),
+                                    dict(max_blocks=3, warp_thresh=4, cta_thresh=64, defer_deg=4, defer_delta=1),
+                                    dict(flags=0x1000)])
+def test_batch_deferred_expansion_matches_oracle(ctx, tuning):
+    """SSSP queries of a batch defer long lists whose vertex is above the query's
+    smallest pushed distance of the last round + defer_delta (every list of at
+    least one edge with defer_deg = 1); with BFS and CC queries in the same
+    batch, every result equals the oracle's, over two runs."""
+    from paper_1607_05707_gb300.api import Batch
+
+    inst = _instances()
+    graphs = [ctx.load(g) for _, g, _ in inst]
+    b = Batch(ctx, 64)
+    for (k, g, s), dg in zip(inst, graphs):
+        b.add(k, dg, s)
+    b.prepare(tuning)
+    for rep in range(2):
+        b.run()
+        for q, (k, g, s) in enumerate(inst):
+            got, _ = b.result(q)
+            np.testing.assert_array_equal(got, oracle.run(k, g, s), err_msg=f"query {q} ({k}) {tuning} rep {rep}")
+    b.close()
+    for dg in graphs:
+        dg.close()
