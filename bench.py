@@ -487,14 +487,27 @@ def run_gpu(args, world, rank, local):
             e1.record(stream)
             st = ctx.sync()
             t, a, o = C.irgl_trace_read(ctx.handle)
+            ph = C.irgl_trace_phases(ctx.handle)
             print(f"# trace {k} source {srcs[used[0]]}: rounds={st['rounds']} total_us={(int(t[-1]) - int(t[0])) / 1e3:.1f}"
                   f" prologue_us={int(o[0]) / 1e3:.2f} event_us={1e3 * e0.elapsed_time(e1):.1f}", file=sys.stderr)
+            print("#  (phase columns: us after the previous round's end; first/last = earliest/latest CTA)",
+                  file=sys.stderr)
+            mask = (1 << 64) - 1
             for r in range(1, len(t)):
                 if int(a[r]) == INF and int(o[r]) == INF:
                     print(f"#  epilogue us {(int(t[r]) - int(t[r - 1])) / 1e3:9.2f}", file=sys.stderr)
                     continue
-                print(f"#  round {r - 1:5d} us {(int(t[r]) - int(t[r - 1])) / 1e3:9.2f} in {int(a[r]):9d} out {int(o[r]):9d}",
-                      file=sys.stderr)
+                line = f"#  round {r - 1:5d} us {(int(t[r]) - int(t[r - 1])) / 1e3:9.2f} in {int(a[r]):9d} out {int(o[r]):9d}"
+                if r - 1 < len(ph) and int(ph[r - 1][1]):
+                    w = [int(x) for x in ph[r - 1]]
+                    t0 = int(t[r - 1])
+                    line += (f" | phase 1 first {((~w[0] & mask) - t0) / 1e3:7.2f} last {(w[1] - t0) / 1e3:7.2f}"
+                             f" | barrier exit {(w[2] - t0) / 1e3:7.2f}")
+                    if w[3]:
+                        line += (f" | big list {w[3] >> 40:6d} lists {w[3] & ((1 << 40) - 1):9d} edges"
+                                 f" first {((~w[4] & mask) - t0) / 1e3:7.2f} last {(w[5] - t0) / 1e3:7.2f}"
+                                 f" barrier exit {(w[6] - t0) / 1e3:7.2f}")
+                print(line, file=sys.stderr)
         C.irgl_trace_enable(ctx.handle, 0)
 
     rec = {k: [] for k in kernels}

@@ -283,11 +283,19 @@ irgl_status irgl_run(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uint32_t
  * Record rounds + 1, when the capacity has room for it, is the end of the
  * epilogue (results written), marked with in = out = 0xFFFFFFFF.
  * irgl_trace_enable(ctx, 0) switches tracing off; enabling allocates 16 bytes
- * per round of capacity. irgl_trace_read copies min(cap, capacity, rounds of
- * the last launch + 2) records. */
+ * per round of capacity, plus 64 for the phase records below. irgl_trace_read
+ * copies min(cap, capacity, rounds of the last launch + 2) records. */
 irgl_status irgl_trace_enable(irgl_ctx* ctx, uint32_t max_rounds);
 irgl_status irgl_trace_read(irgl_ctx* ctx, uint64_t* t_ns, uint32_t* in_n, uint32_t* out_n, uint32_t cap,
                             uint32_t* nrec);
+/* Phase records of the last single-query persistent Iterate (grid-wide kernel),
+ * one per round, 8 words each (globaltimer ns): [0] ~(earliest end of the
+ * round's first phase over all CTAs), [1] its latest end, [2] the time CTA 0
+ * left the first grid barrier, [3] the big list published there ((entries << 40)
+ * | edges; 0 = none), [4] ~(earliest end of the big phase), [5] its latest end,
+ * [6] the time CTA 0 left the second barrier, [7] 0. Copies min(cap, capacity,
+ * rounds) records into `words` (cap * 8 entries). */
+irgl_status irgl_trace_phases(irgl_ctx* ctx, uint64_t* words, uint32_t cap, uint32_t* nrec);
 
 /* ---------------------------------------------------------------- block sizes
  * Sec. 4.4 rule for an outlined Pipe: the control kernel's block size must be

@@ -285,6 +285,7 @@ KParams make_params(irgl_ctx* ctx, irgl_graph* g, uint32_t* state, const irgl_tu
   p.init_state = 1;
   p.trace = ctx->trace;
   p.trace_cap = ctx->trace_cap;
+  p.trace_ph = ctx->trace ? ctx->trace + 2 * (size_t)ctx->trace_cap : nullptr;
   p.big = (t.flags & IRGL_TUNE_NO_SPLIT) ? BigList{nullptr, nullptr, 0} : BigList{ctx->big_e, ctx->big_off, ctx->big_cap};
   if (ctx->dbg_big_cap && p.big.cap > ctx->dbg_big_cap) p.big.cap = ctx->dbg_big_cap;
   // small-frontier rounds pay for their broadcast reads by skipping the big
@@ -408,7 +409,8 @@ irgl_status irgl_trace_enable(irgl_ctx* ctx, uint32_t max_rounds) {
   ctx->trace = nullptr;
   ctx->trace_cap = 0;
   if (max_rounds == 0) return IRGL_OK;
-  const size_t bytes = sizeof(unsigned long long) * 2 * ((size_t)max_rounds + 1);
+  // round records (2 words each), then the phase records (kPhaseWords each)
+  const size_t bytes = sizeof(unsigned long long) * (2 + kPhaseWords) * ((size_t)max_rounds + 1);
   cudaError_t e = cudaMalloc(&ctx->trace, bytes);
   if (e == cudaSuccess) e = cudaMemset(ctx->trace, 0, bytes);
   if (e != cudaSuccess) return cuda_fail(e, "trace allocation");
@@ -433,6 +435,21 @@ irgl_status irgl_trace_read(irgl_ctx* ctx, uint64_t* t_ns, uint32_t* in_n, uint3
     if (in_n) in_n[i] = static_cast<uint32_t>(buf[2 * i + 1] >> 32);
     if (out_n) out_n[i] = static_cast<uint32_t>(buf[2 * i + 1]);
   }
+  *nrec = k;
+  return IRGL_OK;
+}
+
+irgl_status irgl_trace_phases(irgl_ctx* ctx, uint64_t* words, uint32_t cap, uint32_t* nrec) {
+  if (!ctx || !nrec || (cap && !words)) return fail(IRGL_ERR_INVALID_ARG, "NULL argument");
+  *nrec = 0;
+  if (!ctx->trace) return IRGL_OK;
+  DeviceGuard guard(ctx->device);
+  const uint32_t k = std::min(std::min(cap, ctx->trace_cap), ctx->st_host->rounds);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess && k)
+    e = cudaMemcpy(words, ctx->trace + 2 * (size_t)ctx->trace_cap, sizeof(unsigned long long) * kPhaseWords * k,
+                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "trace phases read");
   *nrec = k;
   return IRGL_OK;
 }

@@ -164,6 +164,8 @@ struct KParams {
   int skip_cta;                // test hook: this CTA never reaches the first barrier
   int init_state;              // write the Iterate initial values in the prologue
   unsigned long long* trace;   // optional per-round trace: {end time ns, (in_n << 32) | out_n}
+  // optional per-round phase records (trace_cap records of kPhaseWords words; see trace_phase)
+  unsigned long long* trace_ph;
   uint32_t trace_cap;          // rounds the trace can hold
   BigList big;
   // near-far schedule, SSSP and CC (delta = 0: off)
@@ -1819,12 +1821,15 @@ __device__ __forceinline__ void init_smem(Smem<CTA>& sm) {
 #ifndef IRGL_BOTTOM_UP_J
 #define IRGL_BOTTOM_UP_J 4
 #endif
+#ifndef IRGL_BOTTOM_UP_STEPS
+#define IRGL_BOTTOM_UP_STEPS 4  // two-edge steps per vertex before the warp takes a long in-list
+#endif
 template <int CTA>
 __device__ __forceinline__ void bottom_up_round(const KParams& p, Smem<CTA>& sm, const RoundCtx& rc, uint32_t L,
                                                 uint32_t& edges, const uint32_t* cand, uint32_t cand_n,
                                                 uint32_t* rest, uint32_t* rest_n) {
   constexpr uint32_t J = IRGL_BOTTOM_UP_J;  // vertices per thread per pass
-  constexpr uint32_t kLaneSteps = 4;
+  constexpr uint32_t kLaneSteps = IRGL_BOTTOM_UP_STEPS;
   constexpr uint32_t kChunk = 32 * J;       // vertices per warp pass
   const uint32_t lane = threadIdx.x & 31;
   // candidates: the list the previous bottom-up round left (cand), else every vertex
@@ -2105,6 +2110,25 @@ __device__ __forceinline__ void trace_prologue(unsigned long long* trace, uint32
   }
 }
 
+// Phase record of round r (persistent single-query Iterate, when tracing):
+// words 0/1 the earliest and latest end of the round's first phase over all
+// CTAs (word 0 complemented, both gathered with atomicMax), 2 the time CTA 0
+// left the first grid barrier, 3 the big list published there ((entries << 40)
+// | edges; 0: none), 4/5 the earliest (complemented) and latest end of the big
+// phase, 6 the time CTA 0 left the second barrier. All globaltimer ns.
+constexpr uint32_t kPhaseWords = 8;
+__device__ __forceinline__ unsigned long long* trace_phase(unsigned long long* ph, uint32_t cap, uint32_t r) {
+  return (ph != nullptr && r < cap) ? ph + static_cast<size_t>(kPhaseWords) * r : nullptr;
+}
+__device__ __forceinline__ void trace_phase_end(unsigned long long* rec, uint32_t word) {
+  // called by thread 0 of every CTA after a CTA barrier
+  if (rec != nullptr) {
+    const unsigned long long t = globaltimer_ns();
+    atomicMax(rec + word, ~t);
+    atomicMax(rec + word + 1, t);
+  }
+}
+
 // Record rounds + 1 of a trace: the end of the epilogue (results copied out),
 // marked with in = out = 0xFFFFFFFF.
 __device__ __forceinline__ void trace_end(unsigned long long* trace, uint32_t cap, uint32_t rounds) {
@@ -2157,6 +2181,10 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   }
   if (OP == OP_BFS && p.vis != nullptr) {
     for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < (p.n + 31u) >> 5; i += gridDim.x * CTA) __stcg(p.vis + i, 0u);
+  }
+  if (p.trace_ph != nullptr) {  // phase records gather with atomicMax: clear this launch's
+    for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < p.trace_cap * kPhaseWords; i += gridDim.x * CTA)
+      p.trace_ph[i] = 0ull;
   }
   if (ok) ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
   trace_prologue(p.trace, p.trace_cap, t_start, init_n);
@@ -2283,8 +2311,17 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
       atomicMax(&st->pmin[(r + 1) % 3], ~sm.pmin_cta);
       sm.pmin_cta = kInf;
     }
+    unsigned long long* const ph = trace_phase(p.trace_ph, p.trace_cap, r);
+    if (ph != nullptr) {
+      __syncthreads();
+      if (threadIdx.x == 0) trace_phase_end(ph, 0);
+    }
     ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns, !split && p.big.cap != 0);
     if (!ok) break;
+    if (ph != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+      ph[2] = globaltimer_ns();
+      ph[3] = (sm.pub_flags & kRelBigFlag) ? sm.pub_big : 0ull;
+    }
     if (sm.pub_flags & kRelBigFlag) {
       big_phase<OP, CTA>(g, sm, rc, sm.pub_big);
       if (nf && threadIdx.x == 0 && sm.far_min_cta != kInf) atomicMax(&st->far_min[ftarget], ~sm.far_min_cta);
@@ -2296,8 +2333,13 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
         atomicMax(&st->pmin[(r + 1) % 3], ~sm.pmin_cta);
         sm.pmin_cta = kInf;
       }
+      if (ph != nullptr) {
+        __syncthreads();
+        if (threadIdx.x == 0) trace_phase_end(ph, 4);
+      }
       ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
       if (!ok) break;
+      if (ph != nullptr && blockIdx.x == 0 && threadIdx.x == 0) ph[6] = globaltimer_ns();
     }
     last_out = sm.pub_out;
     rounds = r + 1;

@@ -189,6 +189,7 @@ _SIGS = {
     "irgl_debug_set": [_P, c_int, c_int64],
     "irgl_trace_enable": [_P, c_uint32],
     "irgl_trace_read": [_P, _P, _P, _P, c_uint32, POINTER(c_uint32)],
+    "irgl_trace_phases": [_P, _P, c_uint32, POINTER(c_uint32)],
     "irgl_server_create": [_P, POINTER(irgl_server_config), POINTER(_P)],
     "irgl_server_submit": [_P, _P, c_int, c_uint32, _P, POINTER(c_uint64)],
     "irgl_server_poll": [_P, c_uint64, POINTER(irgl_query_info)],
@@ -461,6 +462,16 @@ def irgl_batch_copy_results(b: int, host_out: int) -> None:
 
 def irgl_trace_enable(ctx: int, max_rounds: int) -> None:
     _check(lib().irgl_trace_enable(ctx, max_rounds))
+
+
+def irgl_trace_phases(ctx: int, cap: int = 1 << 16):
+    """Phase records of the last single-query persistent Iterate: uint64 array (rounds, 8)."""
+    import numpy as np
+
+    w = np.zeros((cap, 8), dtype=np.uint64)
+    n = c_uint32()
+    _check(lib().irgl_trace_phases(ctx, w.ctypes.data, cap, ctypes.byref(n)))
+    return w[: int(n.value)]
 
 
 def irgl_trace_read(ctx: int, cap: int = 1 << 16):

@@ -261,6 +261,42 @@ def test_trace_records_rounds(ctx):
     dg.close()
 
 
+def test_trace_phase_records(ctx):
+    """Phase records of a grid-wide persistent SSSP: per round the first phase
+    ends (earliest <= latest CTA) before CTA 0 leaves the first barrier, the big
+    phase (when a big list was published) after it, all within the round; the
+    big lists' edges are at most the edges the launch scanned, and two launches
+    in a row each leave their own records."""
+    from paper_1607_05707_gb300 import irgl as C
+    from paper_1607_05707_gb300.api import as_u32, trace
+
+    g = inputs.rmat(16, 16, seed=71, weights=True)
+    dg = ctx.load(g)
+    src = inputs.sources(g, 2, seed=72)
+    C.irgl_trace_enable(ctx.handle, 256)
+    mask = (1 << 64) - 1
+    for s in src:
+        out, st = ctx.run("sssp", dg, np.array([s], np.uint32), tuning=dict(flags=0x40))
+        np.testing.assert_array_equal(as_u32(out)[: g.n], oracle.run("sssp", g, np.array([s], np.uint32)))
+        t, a, o = trace(ctx)
+        ph = C.irgl_trace_phases(ctx.handle)
+        assert len(ph) == st["rounds"] > 1
+        big_edges = 0
+        for r in range(st["rounds"]):
+            w = [int(x) for x in ph[r]]
+            start, end = int(t[r]), int(t[r + 1])
+            first, last = ~w[0] & mask, w[1]
+            assert start <= first <= last <= w[2] <= end, (r, start, first, last, w[2], end)
+            if w[3]:
+                big_edges += w[3] & ((1 << 40) - 1)
+                assert w[2] <= (~w[4] & mask) <= w[5] <= w[6] <= end, (r, w)
+            else:
+                assert w[4] == w[5] == w[6] == 0
+        assert big_edges <= st["edges_scanned"]
+    C.irgl_trace_enable(ctx.handle, 0)
+    dg.close()
+
+
 @pytest.mark.parametrize("delta", [0, 32])
 def test_batch_config_sample_near_far(ctx, delta):
     """A sample of the 256-instance R-MAT workload batched with and without per-query near-far."""
