@@ -269,8 +269,9 @@ def source_sha(files) -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel_name: str):
-    """DRAM bytes per launch from a committed ncu capture, only if the kernel's sources are unchanged since."""
+def measured_traffic(kernel_name: str, workload: str):
+    """DRAM bytes per launch from a committed ncu capture of this kernel on this workload, only if the
+    kernel's sources are unchanged since (entries are keyed "kernel@workload")."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
         return None
@@ -278,7 +279,7 @@ def measured_traffic(kernel_name: str):
         d = json.loads(p.read_text())
     except ValueError:
         return None
-    ent = d.get(kernel_name)
+    ent = d.get(f"{kernel_name}@{workload}")
     if not ent or not ent.get("sources"):
         return None
     try:
@@ -555,7 +556,7 @@ def run_gpu(args, world, rank, local):
     dom = max(kernels, key=lambda k: per_kernel[k]["time_s"])
     kname = {"bfs": "k_iterate<BFS>", "sssp": "k_iterate<SSSP>", "cc": "k_iterate<CC>", "cc_jump": "k_iterate<CCJ>"}[dom]
     pk = per_kernel[dom]
-    traffic = measured_traffic(kname)
+    traffic = measured_traffic(kname, args.workload if args.workload != "rmat20" or args.scale == 20 else "")
     roofline = {"bound": "hbm", "achieved": round(pk["achieved_gbs"], 2), "peak": hbm, "unit": "GB/s",
                 "frac": round(pk["achieved_gbs"] / hbm, 4), "traffic": traffic, "kernel": kname,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
@@ -867,7 +868,7 @@ def run_batch(args, world, rank, local, embedded=False):
                     "d2h_bytes_per_step": int(4 * sum(g.n for g, _, _ in inst))},
             "gpu_launches": (3 * info["waves"] + 1) * args.steps,
             "roofline": {"bound": "hbm", "achieved": round(nbytes / t_batch / 1e9, 2), "peak": hbm, "unit": "GB/s",
-                         "frac": round(nbytes / t_batch / 1e9 / hbm, 4), "traffic": measured_traffic("k_batch_iterate"),
+                         "frac": round(nbytes / t_batch / 1e9 / hbm, 4), "traffic": measured_traffic("k_batch_iterate", f"batch{args.instances}-{args.batch_set}"),
                          "kernel": "k_batch_iterate", "bytes_per_launch": int(nbytes)},
             "cpu_baseline": cpu, "clocks": clk,
         }
@@ -1126,7 +1127,7 @@ def run_msf(args, world, rank, local):
                     "d2h_bytes_per_step": 4 * int(len(edges))},
             "gpu_launches": args.steps,
             "roofline": {"bound": "hbm", "achieved": round(nbytes / t_step / 1e9, 2), "peak": hbm, "unit": "GB/s",
-                         "frac": round(nbytes / t_step / 1e9 / hbm, 4), "traffic": measured_traffic("k_msf"),
+                         "frac": round(nbytes / t_step / 1e9 / hbm, 4), "traffic": measured_traffic("k_msf", f"msf-{args.msf_graph}"),
                          "kernel": "k_msf", "bytes_per_launch": int(nbytes),
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
             "lock_forms": forms,
