@@ -364,6 +364,9 @@ irgl_status irgl_ctx_destroy(irgl_ctx* ctx) {
   DeviceGuard guard(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->run_wl) irgl_worklist_destroy(ctx->run_wl);
+  delete ctx->run_src_wl;
+  cudaFree(ctx->run_src);
+  if (ctx->run_src_host) cudaFreeHost(ctx->run_src_host);
   cudaFree(ctx->ws_items[0]);
   cudaFree(ctx->ws_items[1]);
   cudaFree(ctx->ws_stamp);
@@ -1009,7 +1012,28 @@ irgl_status irgl_run(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uint32_t
   for (uint32_t i = 0; i < nsrc; ++i)
     if (srcs_host[i] >= g->n) return fail(IRGL_ERR_INVALID_ARG, "source %u out of range", srcs_host[i]);
   irgl_worklist* init = nullptr;
-  if (nsrc > 0) {
+  if (nsrc > 0 && nsrc <= kRunSrcMax) {
+    // count and sources in one copy (no clear, push kernel or staging copy)
+    if (!ctx->run_src) {
+      cudaError_t e = cudaMalloc(&ctx->run_src, sizeof(uint32_t) * kRunSrcWords);
+      if (e == cudaSuccess) e = cudaMallocHost(&ctx->run_src_host, sizeof(uint32_t) * kRunSrcWords);
+      if (e != cudaSuccess) return cuda_fail(e, "run source buffer");
+      ctx->run_src_wl = new (std::nothrow) irgl_worklist();
+      if (!ctx->run_src_wl) return fail(IRGL_ERR_OOM, "run source worklist");
+      ctx->run_src_wl->ctx = ctx;
+      ctx->run_src_wl->cap = kRunSrcMax;
+      ctx->run_src_wl->tail = ctx->run_src;
+      ctx->run_src_wl->items = ctx->run_src + 32;
+      std::memset(ctx->run_src_host, 0, sizeof(uint32_t) * 32);
+    }
+    // the mirror is free again: every irgl_run waits for its stream before returning
+    ctx->run_src_host[0] = nsrc;
+    std::memcpy(ctx->run_src_host + 32, srcs_host, sizeof(uint32_t) * nsrc);
+    cudaError_t e = cudaMemcpyAsync(ctx->run_src, ctx->run_src_host, sizeof(uint32_t) * (32 + (size_t)nsrc),
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "run sources");
+    init = ctx->run_src_wl;
+  } else if (nsrc > 0) {
     if (!ctx->run_wl || ctx->run_wl->cap < nsrc) {
       if (ctx->run_wl) irgl_worklist_destroy(ctx->run_wl);
       ctx->run_wl = nullptr;
@@ -1042,6 +1066,7 @@ irgl_status irgl_run(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uint32_t
     cudaError_t e = cudaMemcpyAsync(state, dst, sizeof(uint32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "result copy");
     if (mode == IRGL_PERSISTENT) {
+      // one wait for the launch, the result copy and the status read
       DevStatus st;
       s = read_status(ctx, &st);
       if (stats) {
@@ -1049,8 +1074,10 @@ irgl_status irgl_run(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, const uint32_t
         stats->last_out = ctx->st_host->last_out;
         stats->edges_scanned = ctx->st_host->edges;
       }
-      cudaMemsetAsync(&ctx->st->edges, 0, sizeof(unsigned long long), ctx->stream);
       if (s != IRGL_OK) return s;
+      // cleared for the next call; later work on the stream runs after it
+      cudaMemsetAsync(&ctx->st->edges, 0, sizeof(unsigned long long), ctx->stream);
+      return IRGL_OK;
     }
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "result copy");

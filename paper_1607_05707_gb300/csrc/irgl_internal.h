@@ -20,6 +20,9 @@ struct irgl_ctx {
   int smem_optin = 0;  // opt-in shared memory per block (bytes)
   irgl::DevStatus* st = nullptr;       // device status block
   irgl::DevStatus* st_host = nullptr;  // pinned mirror
+  uint32_t* run_src = nullptr;       // irgl_run sources (kRunSrcWords words, device)
+  uint32_t* run_src_host = nullptr;  //   and their pinned mirror
+  irgl_worklist* run_src_wl = nullptr;  // worklist view of run_src (owns nothing)
   uint32_t* ws_items[2] = {nullptr, nullptr};  // Iterate scratch worklists
   uint32_t ws_cap = 0;
   uint4* big_e = nullptr;               // big list of long adjacency lists (persistent kernels)
@@ -79,6 +82,11 @@ struct irgl_worklist {
   uint32_t* staging = nullptr;  // device copy of host items being pushed
   uint32_t staging_n = 0;
 };
+
+// irgl_run's sources: one device block [count, 31 words of padding, items...]
+// written by a single copy from a pinned mirror, viewed as a worklist.
+constexpr uint32_t kRunSrcWords = 1024;
+constexpr uint32_t kRunSrcMax = kRunSrcWords - 32;
 
 namespace irgl {
 
