@@ -1162,10 +1162,11 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
   // Long lists. With the big list on, each warp appends its long lists (one
   // 64-bit atomic reserves slots and edge offsets together); the whole grid
   // walks them after the round's first barrier. A frontier smaller than one
-  // tile per CTA sends every list of warp size or more there (the few CTAs
-  // holding items would otherwise walk them alone). Lists that do not fit the
-  // big list fall back to the warp bin. With the big list off (one-launch
-  // rounds), the CTA bin walks lists >= cta_thresh one at a time.
+  // tile per CTA sends every list of warp size or more there: even spread over
+  // every CTA, a warp walking a list of a few hundred edges alone is slower
+  // than the big phase's equal shares. Lists that do not fit the big list fall
+  // back to the warp bin. With the big list off (one-launch rounds), the CTA
+  // bin walks lists >= cta_thresh one at a time.
   const uint32_t split = (rc.big.cap != 0 && rc.in_n < gridDim.x * CTA) ? min(rc.tn.warp_thresh, rc.tn.cta_thresh)
                                                                          : rc.tn.cta_thresh;
   bool big = valid && deg >= split;
