@@ -1355,7 +1355,8 @@ __device__ __forceinline__ void process_tile(const V& g, Smem<CTA>& sm, const Ro
 
 // ForAll over the in-worklist (Sec. 3.1): the first `chunk` tiles of CTA items
 // of each CTA are static (blockIdx-th span); the rest is grabbed dynamically
-// with one atomic per span, so small frontiers cost no contended atomic.
+// with one atomic per span, so small frontiers cost no contended atomic. A
+// frontier below one tile per CTA is spread over every CTA instead (below).
 template <uint32_t OP, int CTA, int RED, class V>
 __device__ __forceinline__ void round_body(const V& g, Smem<CTA>& sm, const RoundCtx& rc, uint32_t& edges,
                                            uint32_t& any_true, uint32_t& any_false) {
@@ -1813,8 +1814,9 @@ __device__ __forceinline__ void init_smem(Smem<CTA>& sm) {
 // the in-edges scanned until a parent is found. Only a parent at exactly L
 // counts: an unvisited vertex has no visited in-neighbour below L, and one
 // found in this round (L + 1) is not a parent yet. Each thread takes four
-// vertices at once (strided by the CTA size, so every load coalesces) and
-// checks two in-edges of each per step for up to four steps, so eight
+// vertices at once (a warp takes 128 consecutive ones, 32 apart per thread,
+// so every load coalesces) and checks two in-edges of each per step for up
+// to four steps, so eight
 // independent chains of loads are in flight per thread; what is still open
 // after that (in-lists longer than eight) is scanned by the whole warp, 64
 // in-edges per step, so one long list does not hold the warp for hundreds
