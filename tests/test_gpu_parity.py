@@ -256,6 +256,25 @@ def test_many_sources_init_path(ctx):
     dg.close()
 
 
+@pytest.mark.parametrize("nsrc", [1, 992, 993, 3000])
+def test_run_source_block_sizes(ctx, nsrc):
+    """irgl_run passes up to 992 sources in one copy of its source block and more
+    through a worklist push: both sides of the bound, with device and host
+    result buffers and repeated calls, equal the oracle (repeated sources included)."""
+    g = inputs.rmat(13, 8, seed=7, weights=True)
+    dg = ctx.load(g)
+    rng = np.random.default_rng(nsrc)
+    srcs = rng.integers(0, g.n, size=nsrc).astype(np.uint32)
+    for kernel in ("bfs", "sssp"):
+        want = oracle.run(kernel, g, srcs)
+        for rep in range(2):
+            got, _ = run(ctx, kernel, g, dg, srcs)
+            np.testing.assert_array_equal(got, want, err_msg=f"{kernel} device rep {rep}")
+            host, _ = ctx.run_host(kernel, dg, srcs)
+            np.testing.assert_array_equal(host, want, err_msg=f"{kernel} host rep {rep}")
+    dg.close()
+
+
 # ----------------------------------------------------------------------------- Invoke, reductions, worklists
 
 def test_invoke_bulk_synchronous_and_reductions(ctx):
