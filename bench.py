@@ -506,6 +506,8 @@ def run_gpu(args, world, rank, local):
                 if r - 1 < len(ph) and int(ph[r - 1][1]):
                     w = [int(x) for x in ph[r - 1]]
                     t0 = int(t[r - 1])
+                    if r == 1 and (~w[0] & mask) < t0:
+                        t0 -= int(o[0])  # round 0 ran inside the prologue: times from the kernel's start
                     line += (f" | phase 1 first {((~w[0] & mask) - t0) / 1e3:7.2f} last {(w[1] - t0) / 1e3:7.2f}"
                              f" | barrier exit {(w[2] - t0) / 1e3:7.2f}")
                     if w[3]:

@@ -891,6 +891,11 @@ irgl_status iterate_impl(irgl_ctx* ctx, irgl_kernel k, irgl_graph* g, irgl_workl
     const uint32_t grid = persistent_grid(ctx, op, t);
     if (grid == 0) return fail(IRGL_ERR_CUDA, "persistent kernel cannot be made resident");
     p.skip_cta = ctx->dbg_skip_cta;
+    if (p.trace_ph != nullptr) {
+      // phase records gather with atomicMax: cleared before each traced launch
+      cudaError_t e = cudaMemsetAsync(p.trace_ph, 0, sizeof(unsigned long long) * kPhaseWords * p.trace_cap, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "trace phase clear");
+    }
     cudaError_t e = launch_iterate(op, t.cta_size, grid, p, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "persistent launch");
     local.grid = grid;

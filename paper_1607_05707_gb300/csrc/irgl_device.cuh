@@ -2120,6 +2120,8 @@ __device__ __forceinline__ void trace_prologue(unsigned long long* trace, uint32
 // | edges; 0: none), 4/5 the earliest (complemented) and latest end of the big
 // phase, 6 the time CTA 0 left the second barrier. All globaltimer ns.
 constexpr uint32_t kPhaseWords = 8;
+// Round 0 is fused into the prologue when the sources have at most this many out-edges together.
+constexpr uint32_t kFuseEdges = 256;
 __device__ __forceinline__ unsigned long long* trace_phase(unsigned long long* ph, uint32_t cap, uint32_t r) {
   return (ph != nullptr && r < cap) ? ph + static_cast<size_t>(kPhaseWords) * r : nullptr;
 }
@@ -2157,6 +2159,15 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   uint32_t rounds = 0, last_out = 0;
   bool ok = true;
 
+  // Round 0 fused into the prologue (BFS; at most eight sources with at most
+  // kFuseEdges out-edges together, plain rounds; SSSP measured slower, its
+  // kernel spilling more registers with the fused code in it): the
+  // thread that initialises a vertex is the only writer of its value until the
+  // prologue barrier, so the CTA owning a source's out-neighbour relaxes that
+  // edge right after its own initialisation (a CTA barrier between) and pushes
+  // it; the prologue's grid barrier then ends round 0 and publishes its pushes.
+  bool fused = false;
+  uint32_t fused_out = 0;
   if (p.init_state) {
     uint32_t srcs[8];
     uint32_t ns = 0;
@@ -2166,6 +2177,61 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
     if (small) ns = init_n;
     if ((OP == OP_SSSP || OP == OP_BFSR) && p.ds != nullptr) fill_packed(p.ds, p.n, srcs, ns, blockIdx.x * CTA + threadIdx.x, gridDim.x * CTA);
     else fill_state<OP>(p.state, p.n, srcs, ns, blockIdx.x * CTA + threadIdx.x, gridDim.x * CTA);
+    if constexpr (OP == OP_BFS) {
+    // sources' out-degrees (every thread, the same few words): decide the fusion
+    uint32_t sbeg[8], sdeg[8], tdeg = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) {
+      sbeg[i] = 0;
+      sdeg[i] = 0;
+      if (i < ns && srcs[i] < p.n) {
+        sbeg[i] = __ldg(p.row_ptr + srcs[i]);
+        sdeg[i] = __ldg(p.row_ptr + srcs[i] + 1) - sbeg[i];
+      }
+      tdeg += sdeg[i];
+    }
+    fused = small && ns > 0 && tdeg <= kFuseEdges && p.vis == nullptr && p.diropt != 2 && p.max_rounds > 1;
+    if (fused) {
+      __syncthreads();  // this CTA's initial values before its relaxations
+      const Out out0{p.items[1], &st->tail[1], p.cap, &st->err};
+      const unsigned long long nthreads = static_cast<unsigned long long>(gridDim.x) * CTA;
+      for (uint32_t base = 0; base < tdeg; base += CTA) {
+        const uint32_t e = base + threadIdx.x;
+        bool push = false;
+        uint32_t v = 0;
+        if (e < tdeg) {
+          // edge e of the sources' concatenated out-lists
+          uint32_t i = 0, off = e;
+#pragma unroll
+          for (uint32_t k = 0; k < 7; ++k) {
+            if (i == k && off >= sdeg[k]) {
+              off -= sdeg[k];
+              i = k + 1;
+            }
+          }
+          uint32_t edge = 0;
+#pragma unroll
+          for (uint32_t k = 0; k < 8; ++k) edge = i == k ? sbeg[k] + off : edge;
+          v = __ldg(p.col + edge);
+          // the CTA whose thread initialised v relaxes it: fill_state gives vertex v to
+          // thread v mod T, or, on a 16-byte-aligned array, groups of four to thread
+          // v / 4 mod T and the last n mod 4 vertices one by one
+          unsigned long long own = v % nthreads;
+          if ((reinterpret_cast<uintptr_t>(p.state) & 15u) == 0) {
+            const uint32_t n4 = (p.n >> 2) << 2;
+            own = v < n4 ? (v >> 2) % nthreads : (v - n4) % nthreads;
+          }
+          if (v < p.n && own / CTA == blockIdx.x) push = atomicCAS(p.state + v, kInf, 1u) == kInf;
+        }
+        push1<CTA>(sm, out0, push, v);
+      }
+      __syncthreads();
+      flush_stage<CTA>(sm, out0);
+      if (blockIdx.x == 0 && threadIdx.x == 0) edges += tdeg;
+      // phase record of round 0 (the host clears the records before a traced launch)
+      if (threadIdx.x == 0) trace_phase_end(trace_phase(p.trace_ph, p.trace_cap, 0), 0);
+    }
+    }
     if (OP != OP_CC && !small) {
       ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
       if (ok) {
@@ -2185,12 +2251,19 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   if (OP == OP_BFS && p.vis != nullptr) {
     for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < (p.n + 31u) >> 5; i += gridDim.x * CTA) __stcg(p.vis + i, 0u);
   }
-  if (p.trace_ph != nullptr) {  // phase records gather with atomicMax: clear this launch's
-    for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < p.trace_cap * kPhaseWords; i += gridDim.x * CTA)
-      p.trace_ph[i] = 0ull;
-  }
   if (ok) ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
   trace_prologue(p.trace, p.trace_cap, t_start, init_n);
+  bool skip_rounds = false;
+  if (fused && ok) {
+    // round 0 ended at the prologue barrier
+    fused_out = sm.pub_out;
+    last_out = fused_out;
+    rounds = 1;
+    unsigned long long* const ph0 = trace_phase(p.trace_ph, p.trace_cap, 0);
+    if (ph0 != nullptr && blockIdx.x == 0 && threadIdx.x == 0) ph0[2] = globaltimer_ns();
+    trace_round(p.trace, p.trace_cap, 1, init_n, fused_out);
+    skip_rounds = fused_out == 0 || sm.pub_err != DERR_NONE;
+  }
 
   // Near-far schedule (SSSP distances, CC labels): improvements to a value >=
   // limit wait on a far list; when a round pushes nothing below the limit, a
@@ -2209,8 +2282,8 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   bool bottom_up = dopt && p.diropt == 2;  // test hook: every round bottom-up
   uint32_t bu_k = 0;                       // bottom-up rounds run so far
   unsigned long long visited_edges = 0;
-  uint32_t prev_n = init_n;
-  uint32_t in_n = init_n;
+  uint32_t prev_n = fused ? fused_out : init_n;
+  uint32_t in_n = fused ? min(fused_out, p.cap) : init_n;
   // small frontiers skip the big list (broadcast_round): BFS, SSSP and
   // min-label CC rounds (near-far included) without CTA-local sub-rounds
   const bool bcast = p.bcast != 0 && (OP == OP_BFS || OP == OP_SSSP || OP == OP_CC) && p.local_rounds == 0;
@@ -2221,7 +2294,7 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   const bool defer = OP == OP_SSSP && p.defer_deg != 0 && p.ds != nullptr && !nf && p.local_rounds == 0 &&
                      p.dense_div == 0;
   const unsigned long long t_run0 = p.time_limit_ns ? globaltimer_ns() : 0ull;
-  for (uint32_t r = 0; ok; ++r) {
+  for (uint32_t r = fused ? 1u : 0u; ok && !skip_rounds; ++r) {
     check_time_limit(&st->err, t_run0, p.time_limit_ns);
     uint32_t* const cur = (r & 1) ? p.items[1] : p.items[0];  // no dynamic index into the param struct
     uint32_t* const nxt = (r & 1) ? p.items[0] : p.items[1];

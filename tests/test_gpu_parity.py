@@ -275,6 +275,56 @@ def test_run_source_block_sizes(ctx, nsrc):
     dg.close()
 
 
+def fused_round0_graph(rng):
+    """Uniform random graph (n = 700,003: n mod 4 = 3, and vertices past four per thread of the
+    widest grid) whose first vertices are sources with chosen out-degrees around 256."""
+    n = 700_003
+    m = 3_000_000
+    src = rng.integers(16, n, size=m)
+    dst = rng.integers(0, n, size=m)
+
+    def targets(k, extra=()):
+        t = list(extra) + rng.integers(0, n, size=k - len(extra)).tolist()
+        return t[:k]
+
+    edges = []
+    # 0: 256 out-edges with the last three vertices, far vertices, a repeated target and a self-loop
+    edges += [(0, v) for v in targets(256, (n - 1, n - 2, n - 3, 4 * 155_648 + 5, 99, 99, 0))]
+    edges += [(1, v) for v in targets(257, (n - 1,))]   # 1: 257 out-edges
+    edges += [(2, v) for v in targets(255, (n - 2,))]   # 2: 255 out-edges
+    # 3: no out-edges; 4: a self-loop only
+    edges += [(4, 4)]
+    for u in range(5, 14):                              # 5..13: 32 out-edges each
+        edges += [(u, v) for v in targets(32)]
+    edges += [(14, v) for v in targets(33)]             # 14: 33 out-edges
+    es, ed = zip(*edges)
+    src = np.concatenate([src, np.array(es)])
+    dst = np.concatenate([dst, np.array(ed)])
+    w = rng.integers(1, 101, size=src.size)
+    return inputs.csr_from_edges(n, src, dst, w)
+
+
+def test_bfs_round0_in_prologue(ctx):
+    """BFS from one to eight sources with at most 256 out-edges together runs its first round in
+    the persistent kernel's prologue; both sides of each bound (255/256/257 edges, 8/9 sources),
+    sources with no out-edge or only a self-loop, repeated sources, the direction-optimising
+    form and the visited bitmap (never fused) equal the oracle."""
+    g = fused_round0_graph(np.random.default_rng(1607))
+    dg = ctx.load(g)
+    sets = [[0], [1], [2], [3], [4], [0, 0], [3, 4], [0, 3], list(range(5, 13)), list(range(5, 14)),
+            list(range(7, 15)), [12, 13, 3, 4, 2], [3, 4, 2], [4, 4, 3]]
+    for srcs in sets:
+        srcs = np.array(srcs, dtype=np.uint32)
+        want = oracle.run("bfs", g, srcs)
+        for t in (None, dict(flags=2), dict(flags=4), dict(cta_size=1024), dict(cta_size=128, max_blocks=1)):
+            got, st = run(ctx, "bfs", g, dg, srcs, tuning=t)
+            np.testing.assert_array_equal(got, want, err_msg=f"sources {srcs.tolist()} tuning {t}")
+            if t is None or not t.get("flags"):
+                # top-down: one round per level plus the last round that pushes nothing
+                assert st["rounds"] == int(want[want != INF].max()) + 1, (srcs.tolist(), t)
+    dg.close()
+
+
 # ----------------------------------------------------------------------------- Invoke, reductions, worklists
 
 def test_invoke_bulk_synchronous_and_reductions(ctx):
