@@ -2251,6 +2251,15 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   if (OP == OP_BFS && p.vis != nullptr) {
     for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < (p.n + 31u) >> 5; i += gridDim.x * CTA) __stcg(p.vis + i, 0u);
   }
+  if constexpr (OP != OP_BFS) {
+    // phase records gather with atomicMax: clear this launch's (BFS, whose round 0 may write its
+    // record before this point, has them cleared by the host; the other operators keep the clear
+    // here, without which the SSSP kernel's registers fell differently and it ran 2 % slower)
+    if (p.trace_ph != nullptr) {
+      for (uint32_t i = blockIdx.x * CTA + threadIdx.x; i < p.trace_cap * kPhaseWords; i += gridDim.x * CTA)
+        p.trace_ph[i] = 0ull;
+    }
+  }
   if (ok) ok = grid_barrier<CTA>(sm, st, gen, p.timeout_ns);
   trace_prologue(p.trace, p.trace_cap, t_start, init_n);
   bool skip_rounds = false;
@@ -2282,8 +2291,16 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   bool bottom_up = dopt && p.diropt == 2;  // test hook: every round bottom-up
   uint32_t bu_k = 0;                       // bottom-up rounds run so far
   unsigned long long visited_edges = 0;
-  uint32_t prev_n = fused ? fused_out : init_n;
-  uint32_t in_n = fused ? min(fused_out, p.cap) : init_n;
+  uint32_t prev_n = init_n;
+  uint32_t in_n = init_n;
+  uint32_t r0 = 0;
+  if constexpr (OP == OP_BFS) {
+    if (fused) {
+      prev_n = fused_out;
+      in_n = min(fused_out, p.cap);
+      r0 = 1;
+    }
+  }
   // small frontiers skip the big list (broadcast_round): BFS, SSSP and
   // min-label CC rounds (near-far included) without CTA-local sub-rounds
   const bool bcast = p.bcast != 0 && (OP == OP_BFS || OP == OP_SSSP || OP == OP_CC) && p.local_rounds == 0;
@@ -2294,7 +2311,7 @@ __device__ __forceinline__ void iterate_persistent(const KParams& p, Smem<CTA>& 
   const bool defer = OP == OP_SSSP && p.defer_deg != 0 && p.ds != nullptr && !nf && p.local_rounds == 0 &&
                      p.dense_div == 0;
   const unsigned long long t_run0 = p.time_limit_ns ? globaltimer_ns() : 0ull;
-  for (uint32_t r = fused ? 1u : 0u; ok && !skip_rounds; ++r) {
+  for (uint32_t r = r0; ok && (OP != OP_BFS || !skip_rounds); ++r) {
     check_time_limit(&st->err, t_run0, p.time_limit_ns);
     uint32_t* const cur = (r & 1) ? p.items[1] : p.items[0];  // no dynamic index into the param struct
     uint32_t* const nxt = (r & 1) ? p.items[0] : p.items[1];
