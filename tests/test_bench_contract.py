@@ -33,3 +33,33 @@ def test_reference_arm_json_line(args):
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_traffic_entry_used_only_for_unchanged_sources(tmp_path, monkeypatch):
+    """A committed DRAM-traffic figure fills the bench line only while the hashed kernel sources
+    are unchanged; an edited source, a missing entry or a malformed file gives null."""
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_under_test", ROOT / "bench.py")
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    csrc = tmp_path / "paper_1607_05707_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "a.cuh").write_text("kernel a\n")
+    (csrc / "b.cu").write_text("kernel b\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", tmp_path)
+    entry = {"bytes_per_launch": 12345, "sources": ["a.cuh", "b.cu"], "source_sha": bench.source_sha(["a.cuh", "b.cu"])}
+    tj = tmp_path / "profiles" / "traffic.json"
+    tj.write_text(json.dumps({"k@w": entry}))
+    assert bench.measured_traffic("k", "w") == 12345
+    assert bench.measured_traffic("k", "other") is None       # keyed per workload
+    assert bench.measured_traffic("other", "w") is None
+    (csrc / "b.cu").write_text("kernel b, edited\n")
+    assert bench.measured_traffic("k", "w") is None           # stale once a source changes
+    (csrc / "b.cu").write_text("kernel b\n")
+    assert bench.measured_traffic("k", "w") == 12345
+    (csrc / "a.cuh").unlink()
+    assert bench.measured_traffic("k", "w") is None           # a missing source
+    tj.write_text("{not json")
+    assert bench.measured_traffic("k", "w") is None
