@@ -469,8 +469,9 @@ irgl_status irgl_server_destroy(irgl_server* s);
  * beyond, before any GPU work). Every call shares that array and it keeps the
  * last call's contents (each call clears its counters), so calls whose GPU work
  * overlaps race and give wrong results. The first call on a device looks up
- * the array's address with that device current; make it before any stream
- * capture. Synchronises on cuda_stream before returning. */
+ * the array's address with that device current. Every call copies its source
+ * from host memory, reads its status back and synchronises cuda_stream before
+ * returning, so it cannot be captured into a CUDA graph. */
 irgl_status irgl_bfs_noalloc(int device, void* cuda_stream, uint32_t n, uint64_t m, const uint32_t* row_ptr,
                              const uint32_t* col, uint32_t src, uint32_t* level, uint32_t* rounds);
 

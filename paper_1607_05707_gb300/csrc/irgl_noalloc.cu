@@ -17,8 +17,9 @@
 // overlaps (other streams or threads) race on the array and give wrong results.
 // A non-null stream must belong to `device` (checked: IRGL_ERR_INVALID_ARG).
 // The first call on a device looks up the array's device address (with that
-// device current) and caches it; make that first call before any stream
-// capture.
+// device current) and caches it. Every call copies its source from host
+// memory, reads the status block back and synchronises the stream before it
+// returns, so no call can be captured into a CUDA graph.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
