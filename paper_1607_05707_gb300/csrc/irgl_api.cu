@@ -140,7 +140,7 @@ void reset_status(irgl_ctx* ctx) {
 }
 
 // Big-list entries: at most one per popped vertex of a round, capped (a full
-// list sends further long lists to the CTA bin, which is still correct).
+// list sends further long lists to the warp bin, which is still correct).
 uint32_t big_capacity(uint64_t n) { return static_cast<uint32_t>(std::min<uint64_t>(std::max<uint64_t>(n, 1), 1u << 22)); }
 
 cudaError_t alloc_big(uint32_t cap, uint4** e, unsigned long long** off) {
